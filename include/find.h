@@ -1,0 +1,150 @@
+/*
+ * find.h -- C ABI of the GB300 FIND selected-inversion library.
+ *
+ * FIND (Fast Inverse using Nested Dissection; Li & Darve, "Extension and
+ * optimization of the FIND algorithm") computes selected entries of
+ *     G  = A^{-1}                     (Sec. 2)
+ *     G< = A^{-1} Sigma< A^{-H}        (Sec. 3.1, Eq. 5)
+ * for the sparse matrix of a 2D Nx x Ny tight-binding mesh
+ *     A = E I - H - Sigma_L - Sigma_R  (Sec. 1; E is complex, eta included)
+ * by an upward pass (Procedure updateBoundaryNodes), a downward pass
+ * (Procedure updateAdjacentNodes) and per-leaf extraction (Procedure
+ * computeG<, Eqs. 8-10), all run as CUDA kernels on one GPU.
+ *
+ * Conventions shared by every call
+ *   - node n = y * nx + x; x in [0, nx) is transverse, y in [0, ny) is the
+ *     transport direction; the leads attach to the columns y = 0 (left) and
+ *     y = ny - 1 (right), nx nodes each.
+ *   - H: onsite0 + V_n on the diagonal, -t to the 4 nearest neighbours,
+ *     -tp to the 4 diagonal neighbours (stencil 9 only).
+ *   - complex numbers are interleaved (re, im) pairs of double; "k complex"
+ *     below means 2k doubles.
+ *   - array pointers may be HOST or DEVICE memory; the library asks the CUDA
+ *     runtime which one it is.  Host inputs are staged to the device on the
+ *     given stream; host outputs are copied back and the call returns after
+ *     the stream has reached them.  With device pointers the call is
+ *     asynchronous on `stream` and its status reflects launch errors only;
+ *     numerical status (singular pivot) is read back at the end of the call.
+ *   - ownership: the caller owns every array it passes; the handle owns the
+ *     plan, the index tables and the resident U/R workspace.
+ *   - errors: every call returns a FIND_* status; no partial outputs are
+ *     promised on error; find_last_error() holds a message for the handle's
+ *     last failing call.  Nothing aborts the process.
+ */
+#ifndef FIND_GB300_H
+#define FIND_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FIND_OK = 0,
+  FIND_EINVAL = 1,     /* bad argument: sizes, stencil, NULL where required */
+  FIND_ENOMEM = 2,     /* device or host allocation failed                  */
+  FIND_ESINGULAR = 3,  /* an exactly zero pivot was met (energy in message) */
+  FIND_ETIMEOUT = 4,   /* a bounded device wait ran out                     */
+  FIND_ECUDA = 5       /* any other CUDA runtime error                      */
+};
+
+enum { FIND_FP64 = 0 };
+
+typedef struct find_handle find_handle;
+
+typedef struct {
+  int nx, ny;               /* mesh size, nx >= 1, ny >= 2                     */
+  int stencil;              /* 5 or 9                                          */
+  double t, tp;             /* nearest and diagonal hopping (tp used if 9)     */
+  const double* onsite_V;   /* nx*ny doubles (host or device), copied at
+                               find_create; NULL means V = 0                   */
+  double onsite0;           /* clean onsite energy (4t, or 4t + 4tp for 9)     */
+  int leaf;                 /* leaf clusters have both sides <= leaf; 0 = 8    */
+  int precision;            /* FIND_FP64                                       */
+  int device;               /* CUDA device ordinal                             */
+  int max_batch;            /* energies solved together; 0 = chosen from free
+                               device memory                                   */
+} find_desc;
+
+/* Host-side facts of the plan (no GPU needed). */
+typedef struct {
+  int n_clusters;           /* basic clusters in the tree (root included)     */
+  int n_leaves;
+  int n_up_levels;          /* upward groups (by height)                       */
+  int n_down_levels;        /* downward groups (by depth)                      */
+  int max_s, max_b;         /* largest private-inner and boundary set          */
+  int max_kn;               /* largest bordered leaf system |Bbar u C|         */
+  int n_bonds;              /* bond-current outputs per energy                 */
+  double flops_diag;        /* algorithmic real flops per energy, diag(G)     */
+  double flops_lesser;      /* algorithmic real flops per energy, diag(G),
+                               diag(G<) and bond currents                      */
+  double ur_bytes;          /* resident U and R bytes per energy               */
+  double scratch_bytes;     /* largest per-level scratch bytes per energy      */
+} find_plan_stats;
+
+/*
+ * Build the nested-dissection tree (Sec. 2.1: bisect the longer side, ties
+ * split y, first half floor(len/2)), the boundary sets B_C = {i in C with a
+ * neighbour outside C}, the complement sets B_Cbar, the private inner sets
+ * S_C = (B_C1 u B_C2) \ B_C, and the gather tables of every merge.
+ * Touches no GPU; device memory is allocated by the first solve.
+ * Returns FIND_EINVAL for nx < 1, ny < 2, a stencil other than 5 or 9, or a
+ * set larger than the kernels support (2048).
+ */
+int find_create(const find_desc* desc, find_handle** out);
+
+/* Plan facts; valid on any machine. */
+int find_plan_info(const find_handle* h, find_plan_stats* out);
+
+/* Bytes of device workspace a solve with `batch` energies per pass uses. */
+int find_workspace_bytes(const find_handle* h, int batch, int lesser, double* bytes);
+
+/*
+ * diag(G) for nE energies (Sec. 2; Eq. 2 in both passes, Eq. 8 at leaves).
+ *   E       nE complex energies (eta included in the imaginary part)
+ *   sigmaL  nE*nx*nx complex, row-major per energy: Sigma_L on column y=0,
+ *           or NULL for the semi-infinite clean-lead closed form
+ *           Phi diag(sigma_m) Phi^T (sine modes; sigma_m the root of
+ *           sigma^2 - (E - eps_m) sigma + tau_m^2 = 0 with |sigma_m| < |tau_m|)
+ *   sigmaR  same for Sigma_R on column y = ny-1 (NULL: closed form)
+ *   diagG   out, nE*nx*ny complex, energy-major
+ *   stream  cudaStream_t (NULL = legacy default stream)
+ */
+int find_solve_diag(find_handle* h, const double* E, int nE,
+                    const double* sigmaL, const double* sigmaR,
+                    double* diagG, void* stream);
+
+/*
+ * diag(G), diag(G<) and bond currents (Sec. 3.1 Eqs. 5 and 7; Sec. 3.2).
+ *   Sigma< = i (fL Gamma_L + fR Gamma_R) + diag(d), Gamma = i (Sigma - Sigma^H)
+ *   sigma_lesser_diag  NULL, or node-diagonal d: nx*ny complex shared by all
+ *                      energies (diag_per_energy = 0) or nE*nx*ny complex
+ *                      (diag_per_energy = 1)
+ *   diagG, diagGl      out, nE*nx*ny complex each
+ *   bond_current       out or NULL: nE*n_bonds doubles, bond i->j current
+ *                      J = H_ij G<_ji - G<_ij H_ji, evaluated as
+ *                      -2 H_ij Re G<_ij (exact when Sigma< is anti-Hermitian,
+ *                      i.e. real fL, fR and imaginary d).  Bond order per
+ *                      energy: y-bonds (x,y)->(x,y+1) [y*nx+x, y<ny-1];
+ *                      x-bonds (x,y)->(x+1,y) [y*(nx-1)+x]; stencil 9 adds
+ *                      (x,y)->(x+1,y+1) and (x+1,y)->(x,y+1)
+ *                      [y*(nx-1)+x, y<ny-1] in that order.
+ */
+int find_solve_lesser(find_handle* h, const double* E, int nE,
+                      const double* sigmaL, const double* sigmaR,
+                      double fL, double fR,
+                      const double* sigma_lesser_diag, int diag_per_energy,
+                      double* diagG, double* diagGl, double* bond_current,
+                      void* stream);
+
+/* Free the plan and the device workspace.  NULL is accepted. */
+int find_destroy(find_handle* h);
+
+/* Message of the handle's last failing call ("" if none); NULL handle gives
+ * the message of the last failing find_create on this thread. */
+const char* find_last_error(const find_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIND_GB300_H */

@@ -1,0 +1,126 @@
+"""GB300 FIND: selected inversion of A = E I - H - Sigma on 2D meshes.
+
+The compute runs in libfind_gb300.so (hand-written sm_103a CUDA behind the C
+ABI of include/find.h).  This module only marshals arguments: it allocates
+outputs with PyTorch (device memory) or numpy (host memory) and passes raw
+pointers and the current CUDA stream.  There is no CPU fallback: if the
+library is missing, importing the binding raises.
+
+    f = Find(nx=40, ny=40, V=v)            # plan only, no GPU touched
+    dG = f.solve_diag(E)                   # E: complex128 torch (cuda) or numpy
+    dG, dGl, J = f.solve_lesser(E, fL=1.0, fR=0.0)
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import (FIND_FP64, FindError, find_create, find_destroy, find_last_error,  # noqa: F401
+                   find_plan_info, find_solve_diag, find_solve_lesser, find_workspace_bytes)
+
+__all__ = ["Find", "FindError", "find_create", "find_destroy", "find_last_error", "find_plan_info",
+           "find_solve_diag", "find_solve_lesser", "find_workspace_bytes"]
+
+
+def _ptr(x, dtype_name):
+    """Raw data pointer of a contiguous torch tensor or numpy array (or None)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"] or x.dtype.name != dtype_name:
+            raise TypeError(f"expected a C-contiguous {dtype_name} array")
+        return x.ctypes.data
+    import torch
+    want = {"complex128": torch.complex128, "float64": torch.float64}[dtype_name]
+    if not isinstance(x, torch.Tensor) or x.dtype != want or not x.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype_name} tensor")
+    return x.data_ptr()
+
+
+class Find:
+    """One mesh: plan built at construction, device workspace kept resident."""
+
+    def __init__(self, nx, ny, stencil=5, t=1.0, tp=0.0, V=None, onsite0=None, leaf=8,
+                 device=0, max_batch=0):
+        _abi.load()
+        self.nx, self.ny, self.stencil = int(nx), int(ny), int(stencil)
+        self.n = self.nx * self.ny
+        self.t, self.tp = float(t), float(tp)
+        if onsite0 is None:
+            onsite0 = 4.0 * t + (4.0 * tp if stencil == 9 else 0.0)
+        self._V = None if V is None else np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(-1))
+        if self._V is not None and self._V.size != self.n:
+            raise ValueError("V must have nx*ny entries")
+        self.device = int(device)
+        d = _abi.find_desc(self.nx, self.ny, self.stencil, self.t, self.tp,
+                           None if self._V is None else self._V.ctypes.data, float(onsite0),
+                           int(leaf), FIND_FP64, self.device, int(max_batch))
+        self.handle = find_create(d)
+        self.stats = find_plan_info(self.handle)
+        self.n_bonds = self.stats.n_bonds
+
+    @classmethod
+    def from_mesh(cls, mesh, V=None, **kw):
+        return cls(mesh.nx, mesh.ny, mesh.stencil, mesh.t, mesh.tp,
+                   mesh.potential() if V is None else V, mesh.onsite0, **kw)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            find_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers
+    def _stream(self, stream):
+        if stream is not None:
+            return stream
+        import torch
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def _out(self, like, shape, dtype):
+        if isinstance(like, np.ndarray):
+            return np.empty(shape, dtype=dtype)
+        import torch
+        tdt = {np.complex128: torch.complex128, np.float64: torch.float64}[dtype]
+        return torch.empty(shape, dtype=tdt, device=f"cuda:{self.device}")
+
+    def solve_diag(self, E, sigmaL=None, sigmaR=None, stream=None, out=None):
+        """diag(G) for every energy in E -> (nE, nx*ny) complex128."""
+        nE = int(E.shape[0])
+        out = self._out(E, (nE, self.n), np.complex128) if out is None else out
+        find_solve_diag(self.handle, _ptr(E, "complex128"), nE, _ptr(sigmaL, "complex128"),
+                        _ptr(sigmaR, "complex128"), _ptr(out, "complex128"), self._stream(stream))
+        return out
+
+    def solve_lesser(self, E, fL=1.0, fR=0.0, sigmaL=None, sigmaR=None, sigma_lesser_diag=None,
+                     bonds=True, stream=None, out=None):
+        """diag(G), diag(G<) and (optionally) bond currents for every energy."""
+        nE = int(E.shape[0])
+        if out is None:
+            dG = self._out(E, (nE, self.n), np.complex128)
+            dGl = self._out(E, (nE, self.n), np.complex128)
+            J = self._out(E, (nE, self.n_bonds), np.float64) if bonds else None
+        else:
+            dG, dGl, J = out
+        per_e = 0
+        if sigma_lesser_diag is not None:
+            per_e = 1 if sigma_lesser_diag.ndim == 2 else 0
+        find_solve_lesser(self.handle, _ptr(E, "complex128"), nE, _ptr(sigmaL, "complex128"),
+                          _ptr(sigmaR, "complex128"), fL, fR, _ptr(sigma_lesser_diag, "complex128"),
+                          per_e, _ptr(dG, "complex128"), _ptr(dGl, "complex128"),
+                          _ptr(J, "float64"), self._stream(stream))
+        return dG, dGl, J
+
+    def workspace_bytes(self, batch, lesser=True):
+        return find_workspace_bytes(self.handle, batch, lesser)
+
+
+_ = ctypes  # the binding is ctypes-only

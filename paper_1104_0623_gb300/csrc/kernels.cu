@@ -1,0 +1,439 @@
+// CUDA kernels of the FIND passes (FP64 complex).
+//
+//   k_lead_modes / k_lead_dense  lead self-energy closed form (per energy)
+//   k_assemble    gather M = [U_1 A_12; A_21 U_2] (and Sigma_M) ordered [S, B]
+//                 (Procedures updateBoundaryNodes / updateAdjacentNodes)
+//   k_invert      pivoted Gauss-Jordan inverse of M(S,S) in place
+//   k_zgemm       grouped complex GEMM: L = M(B,S) M(S,S)^{-1} (Eq. 13),
+//                 U = M(B,B) - L M(S,B) (Eq. 2),
+//                 R = Sigma(B,B) - L Sigma(S,B) + (L Sigma(S,S) - Sigma(B,S)) L^H
+//                 (Eq. 7 regrouped), and the leaf products G_K Sigma_K G_K^H
+//   k_extract     diag G, diag G<, bond currents from the bordered leaves
+#include "kernels.cuh"
+
+#include <cfloat>
+#include <climits>
+
+namespace findgb {
+
+// ---------------------------------------------------------------- complex helpers
+__device__ __forceinline__ cplx cmk(double x, double y) { return make_double2(x, y); }
+__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return cmk(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ cplx csub(cplx a, cplx b) { return cmk(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+  return cmk(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ cplx cconj(cplx a) { return cmk(a.x, -a.y); }
+__device__ __forceinline__ cplx cscale(cplx a, double s) { return cmk(a.x * s, a.y * s); }
+// c + a * b with four fused multiply-adds
+__device__ __forceinline__ cplx cfma(cplx a, cplx b, cplx c) {
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+// c - a * b
+__device__ __forceinline__ cplx cfms(cplx a, cplx b, cplx c) {
+  c.x = fma(-a.x, b.x, c.x);
+  c.x = fma(a.y, b.y, c.x);
+  c.y = fma(-a.x, b.y, c.y);
+  c.y = fma(-a.y, b.x, c.y);
+  return c;
+}
+// 1 / z by Smith's scaled algorithm (R. L. Smith, CACM 5(8), 1962): divide by
+// the larger of |re|, |im| first so that no intermediate overflows.
+__device__ __forceinline__ cplx crecip(cplx z) {
+  double a = z.x, b = z.y;
+  if (fabs(a) >= fabs(b)) {
+    double r = b / a, d = a + b * r;
+    return cmk(1.0 / d, -r / d);
+  } else {
+    double r = a / b, d = a * r + b;
+    return cmk(r / d, -1.0 / d);
+  }
+}
+// principal square root from the polar half-angle identities
+__device__ __forceinline__ cplx csqrt_principal(cplx z) {
+  double r = hypot(z.x, z.y);
+  if (r == 0.0) return cmk(0.0, 0.0);
+  double t = sqrt(0.5 * (r + fabs(z.x)));
+  if (z.x >= 0.0) return cmk(t, z.y / (2.0 * t));
+  return cmk(fabs(z.y) / (2.0 * t), copysign(t, z.y));
+}
+
+// ---------------------------------------------------------------- lead self-energy
+// sigma_m(E): root of sigma^2 - (E - eps_m) sigma + tau_m^2 = 0 with |sigma| < |tau|.
+__global__ void k_lead_modes(const cplx* __restrict__ E, int nE, const double* __restrict__ eps,
+                             const double* __restrict__ tau, int nx, cplx* __restrict__ out) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nE * nx) return;
+  int e = idx / nx, m = idx % nx;
+  cplx w = cmk(E[e].x - eps[m], E[e].y);
+  double t2 = tau[m] * tau[m];
+  cplx disc = cmk(w.x * w.x - w.y * w.y - 4.0 * t2, 2.0 * w.x * w.y);
+  cplx d = csqrt_principal(disc);
+  cplx r1 = cscale(cadd(w, d), 0.5), r2 = cscale(csub(w, d), 0.5);
+  double a1 = r1.x * r1.x + r1.y * r1.y, a2 = r2.x * r2.x + r2.y * r2.y;
+  out[idx] = (a1 < a2) ? r1 : r2;
+}
+
+// Sigma[e][x1][x2] = sum_m phi[x1][m] sigma[e][m] phi[x2][m]
+__global__ void k_lead_dense(const cplx* __restrict__ sig, const double* __restrict__ phi, int nx,
+                             cplx* __restrict__ out) {
+  int e = blockIdx.y;
+  int x1 = blockIdx.x;
+  const cplx* s = sig + (int64_t)e * nx;
+  for (int x2 = threadIdx.x; x2 < nx; x2 += blockDim.x) {
+    cplx acc = cmk(0, 0);
+    for (int m = 0; m < nx; ++m) {
+      double w = phi[x1 * nx + m] * phi[x2 * nx + m];
+      acc.x = fma(w, s[m].x, acc.x);
+      acc.y = fma(w, s[m].y, acc.y);
+    }
+    out[((int64_t)e * nx + x1) * nx + x2] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- original entries
+// A_ij = E delta_ij - H_ij - Sigma_L,ij - Sigma_R,ij  (Sec. 1)
+__device__ __forceinline__ cplx a_orig(const DevProblem& P, int e, int i, int j) {
+  const int nx = P.nx;
+  int xi = i % nx, yi = i / nx, xj = j % nx, yj = j / nx;
+  cplx v = cmk(0, 0);
+  if (i == j) {
+    v = cmk(P.E[e].x - (P.onsite0 + P.V[i]), P.E[e].y);
+  } else {
+    int dx = abs(xi - xj), dy = abs(yi - yj);
+    if (dx + dy == 1) v.x = P.t;
+    else if (P.stencil == 9 && dx == 1 && dy == 1) v.x = P.tp;
+  }
+  if (yi == 0 && yj == 0) v = csub(v, P.sigL[((int64_t)e * nx + xi) * nx + xj]);
+  if (yi == P.ny - 1 && yj == P.ny - 1) v = csub(v, P.sigR[((int64_t)e * nx + xi) * nx + xj]);
+  return v;
+}
+
+// Sigma<_ij = i (fL Gamma_L + fR Gamma_R)_ij + d_i delta_ij, Gamma = i (Sigma - Sigma^H)
+__device__ __forceinline__ cplx s_orig(const DevProblem& P, int e, int i, int j) {
+  const int nx = P.nx;
+  int xi = i % nx, yi = i / nx, xj = j % nx, yj = j / nx;
+  cplx v = cmk(0, 0);
+  if (yi == 0 && yj == 0) {
+    cplx a = P.sigL[((int64_t)e * nx + xi) * nx + xj];
+    cplx b = P.sigL[((int64_t)e * nx + xj) * nx + xi];
+    v = cadd(v, cscale(csub(a, cconj(b)), -P.fL));
+  }
+  if (yi == P.ny - 1 && yj == P.ny - 1) {
+    cplx a = P.sigR[((int64_t)e * nx + xi) * nx + xj];
+    cplx b = P.sigR[((int64_t)e * nx + xj) * nx + xi];
+    v = cadd(v, cscale(csub(a, cconj(b)), -P.fR));
+  }
+  if (i == j && P.dles) v = cadd(v, P.dles[(int64_t)e * P.dles_estride + i]);
+  return v;
+}
+
+// ---------------------------------------------------------------- assembly
+__global__ void __launch_bounds__(256) k_assemble(const AsmOp* __restrict__ ops,
+                                                  const int* __restrict__ row_op,
+                                                  const Pos* __restrict__ pos, DevProblem P,
+                                                  int lesser) {
+  const int r = blockIdx.x, e = blockIdx.y;
+  const AsmOp& op = ops[row_op[r]];
+  const int n = op.n;
+  const int p = r - op.row0;
+  const Pos pp = pos[op.pos + p];
+  cplx* Mrow = op.M + (int64_t)e * op.estride + (int64_t)p * n;
+  cplx* Srow = Mrow + (int64_t)n * n;
+  const cplx* U = nullptr;
+  const cplx* R = nullptr;
+  int d = 0;
+  if (pp.src == 1) {
+    d = op.d1;
+    U = op.u1 + (int64_t)e * d * d + (int64_t)pp.idx * d;
+    R = op.r1 ? op.r1 + (int64_t)e * d * d + (int64_t)pp.idx * d : nullptr;
+  } else if (pp.src == 2) {
+    d = op.d2;
+    U = op.u2 + (int64_t)e * d * d + (int64_t)pp.idx * d;
+    R = op.r2 ? op.r2 + (int64_t)e * d * d + (int64_t)pp.idx * d : nullptr;
+  }
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const Pos pq = pos[op.pos + q];
+    if (pp.src != 0 && pq.src == pp.src) {
+      Mrow[q] = U[pq.idx];
+      if (lesser) Srow[q] = R[pq.idx];
+    } else {
+      Mrow[q] = a_orig(P, e, pp.node, pq.node);
+      if (lesser) Srow[q] = s_orig(P, e, pp.node, pq.node);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- inversion
+// Gauss-Jordan with partial pivoting (largest |re| + |im|, first index on
+// ties), in place; one CTA per (op, energy).  An exactly zero pivot records
+// the energy in *status and continues with a zero reciprocal.
+constexpr int kInvThreads = 512;
+
+__global__ void __launch_bounds__(kInvThreads) k_invert(const InvOp* __restrict__ ops,
+                                                        int* __restrict__ status, int e_base) {
+  const InvOp op = ops[blockIdx.x];
+  const int e = blockIdx.y;
+  const int s = op.s, ld = op.ld;
+  if (s == 0) return;
+  cplx* a = op.M + (int64_t)e * op.estride;
+  extern __shared__ double2 inv_smem[];
+  cplx* colk = inv_smem;
+  cplx* rowk = colk + s;
+  int* piv = reinterpret_cast<int*>(rowk + s);
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int sh_p;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+
+  for (int k = 0; k < s; ++k) {
+    // pivot search in column k, rows k..s-1
+    double best = -1.0;
+    int bi = INT_MAX;
+    for (int i = k + tid; i < s; i += blockDim.x) {
+      cplx v = a[(int64_t)i * ld + k];
+      double mg = fabs(v.x) + fabs(v.y);
+      if (mg > best) { best = mg; bi = i; }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      double ob = __shfl_down_sync(0xffffffffu, best, off);
+      int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < nwarp ? red_v[lane] : -1.0;
+      bi = lane < nwarp ? red_i[lane] : INT_MAX;
+      for (int off = 16; off > 0; off >>= 1) {
+        double ob = __shfl_down_sync(0xffffffffu, best, off);
+        int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        if (bi == INT_MAX) bi = k;
+        sh_p = bi;
+        piv[k] = bi;
+      }
+    }
+    __syncthreads();
+    const int p = sh_p;
+    if (p != k)
+      for (int j = tid; j < s; j += blockDim.x) {
+        cplx t0 = a[(int64_t)k * ld + j];
+        a[(int64_t)k * ld + j] = a[(int64_t)p * ld + j];
+        a[(int64_t)p * ld + j] = t0;
+      }
+    __syncthreads();
+    cplx pv = a[(int64_t)k * ld + k];
+    cplx pinv;
+    if (pv.x == 0.0 && pv.y == 0.0) {
+      pinv = cmk(0, 0);
+      if (tid == 0) atomicMin(status, e_base + e);
+    } else {
+      pinv = crecip(pv);
+    }
+    __syncthreads();  // every thread has read the pivot before row k changes
+    for (int j = tid; j < s; j += blockDim.x) {
+      cplx v = (j == k) ? pinv : cmul(a[(int64_t)k * ld + j], pinv);
+      rowk[j] = v;
+      a[(int64_t)k * ld + j] = v;
+    }
+    for (int i = tid; i < s; i += blockDim.x) colk[i] = (i == k) ? cmk(0, 0) : a[(int64_t)i * ld + k];
+    __syncthreads();
+    for (int i = warp; i < s; i += nwarp) {
+      if (i == k) continue;
+      const cplx f = colk[i];
+      cplx* row = a + (int64_t)i * ld;
+      for (int j = lane; j < s; j += 32) {
+        cplx v = (j == k) ? cmk(0, 0) : row[j];
+        row[j] = cfms(f, rowk[j], v);
+      }
+    }
+    __syncthreads();
+  }
+  // undo the row interchanges as column interchanges, last first
+  for (int k = s - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int i = tid; i < s; i += blockDim.x) {
+        cplx t0 = a[(int64_t)i * ld + k];
+        a[(int64_t)i * ld + k] = a[(int64_t)i * ld + p];
+        a[(int64_t)i * ld + p] = t0;
+      }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- grouped ZGEMM
+// Tile BM x BN per CTA, BK deep; each thread owns a 4 x 4 block of outputs at
+// rows ty + i*BM/4, cols tx + j*BN/4.  alpha is folded into the A tile.
+template <int BM, int BN, int BK>
+__global__ void __launch_bounds__((BM / 4) * (BN / 4)) k_zgemm(const GemmOp* __restrict__ ops,
+                                                               const int* __restrict__ tile_op) {
+  constexpr int NT = (BM / 4) * (BN / 4);
+  constexpr int RS = BM / 4, CS = BN / 4;
+  __shared__ cplx As[BK][BM + 1];
+  __shared__ cplx Bs[BK][BN + 1];
+  const int t = blockIdx.x, e = blockIdx.y;
+  const GemmOp& op = ops[tile_op[t]];
+  const int local = t - op.tile0;
+  const int m0 = (local / op.tiles_n) * BM, n0 = (local % op.tiles_n) * BN;
+  const int tx = threadIdx.x % CS, ty = threadIdx.x / CS;
+  const int M = op.m, N = op.n;
+  cplx acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = cmk(0, 0);
+
+  for (int pass = 0; pass < 2; ++pass) {
+    const cplx* A = pass ? op.A2 : op.A;
+    const cplx* B = pass ? op.B2 : op.B;
+    const int K = pass ? op.k2 : op.k;
+    if (A == nullptr || K == 0) continue;
+    const int lda = pass ? op.lda2 : op.lda, ldb = pass ? op.ldb2 : op.ldb;
+    const int opb = pass ? op.opb2 : op.opb;
+    const double alpha = pass ? op.alpha2 : op.alpha;
+    A += (int64_t)e * (pass ? op.sa2 : op.sa);
+    B += (int64_t)e * (pass ? op.sb2 : op.sb);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+      for (int idx = threadIdx.x; idx < BM * BK; idx += NT) {
+        int i = idx / BK, kk = idx % BK;
+        int gi = m0 + i, gk = k0 + kk;
+        cplx v = (gi < M && gk < K) ? A[(int64_t)gi * lda + gk] : cmk(0, 0);
+        As[kk][i] = cscale(v, alpha);
+      }
+      if (opb == 0) {
+        for (int idx = threadIdx.x; idx < BK * BN; idx += NT) {
+          int kk = idx / BN, j = idx % BN;
+          int gk = k0 + kk, gj = n0 + j;
+          Bs[kk][j] = (gk < K && gj < N) ? B[(int64_t)gk * ldb + gj] : cmk(0, 0);
+        }
+      } else {
+        for (int idx = threadIdx.x; idx < BK * BN; idx += NT) {
+          int j = idx / BK, kk = idx % BK;
+          int gk = k0 + kk, gj = n0 + j;
+          Bs[kk][j] = (gk < K && gj < N) ? cconj(B[(int64_t)gj * ldb + gk]) : cmk(0, 0);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        cplx av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + i * RS];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + j * CS];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = cfma(av[i], bv[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+  const cplx* C = op.C ? op.C + (int64_t)e * op.sc : nullptr;
+  cplx* D = op.D + (int64_t)e * op.sd;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int gi = m0 + ty + i * RS;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gj = n0 + tx + j * CS;
+      if (gj >= N) continue;
+      cplx v = acc[i][j];
+      if (C) {
+        cplx c = C[(int64_t)gi * op.ldc + gj];
+        v.x = fma(op.beta, c.x, v.x);
+        v.y = fma(op.beta, c.y, v.y);
+      }
+      D[(int64_t)gi * op.ldd + gj] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- leaf extraction
+__global__ void __launch_bounds__(256) k_extract(const ExtractOp* __restrict__ ops,
+                                                 const LeafBond* __restrict__ bonds, DevProblem P,
+                                                 int lesser, int want_bonds, cplx* __restrict__ diagG,
+                                                 cplx* __restrict__ diagGl, double* __restrict__ J,
+                                                 int64_t n_nodes, int64_t n_bonds) {
+  const ExtractOp op = ops[blockIdx.x];
+  const int e = blockIdx.y;
+  const cplx* K = op.K + (int64_t)e * op.estride;
+  const cplx* Q = op.Q + (int64_t)e * op.estride;
+  for (int i = threadIdx.x; i < op.c; i += blockDim.x) {
+    int node = (op.y0 + i / op.wx) * P.nx + op.x0 + i % op.wx;
+    int kk = op.nb + i;
+    diagG[(int64_t)e * n_nodes + node] = K[(int64_t)kk * op.n + kk];
+    if (lesser) diagGl[(int64_t)e * n_nodes + node] = Q[(int64_t)i * op.n + kk];
+  }
+  if (lesser && want_bonds)
+    for (int b = threadIdx.x; b < op.nbond; b += blockDim.x) {
+      const LeafBond lb = bonds[op.bond + b];
+      cplx g = Q[(int64_t)(lb.pi - op.nb) * op.n + lb.pj];
+      double h = lb.kind ? -P.tp : -P.t;  // H_ij of the bond
+      J[(int64_t)e * n_bonds + lb.bond] = -2.0 * h * g.x;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+void launch_lead_modes(const cplx* E, int nE, const double* eps, const double* tau, int nx,
+                       cplx* sig_modes, cudaStream_t st) {
+  int total = nE * nx;
+  k_lead_modes<<<(total + 255) / 256, 256, 0, st>>>(E, nE, eps, tau, nx, sig_modes);
+}
+
+void launch_lead_dense(const cplx* sig_modes, const double* phi, int nx, int nE, cplx* out,
+                       cudaStream_t st) {
+  dim3 grid(nx, nE);
+  k_lead_dense<<<grid, 128, 0, st>>>(sig_modes, phi, nx, out);
+}
+
+void launch_assemble(const AsmOp* ops, const int* row_op, int nrows, const Pos* pos,
+                     const DevProblem& P, int lesser, int nE, cudaStream_t st) {
+  if (nrows == 0) return;
+  dim3 grid(nrows, nE);
+  k_assemble<<<grid, 256, 0, st>>>(ops, row_op, pos, P, lesser);
+}
+
+void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
+                   cudaStream_t st) {
+  if (nops == 0 || max_s == 0) return;
+  size_t smem = (size_t)max_s * (2 * sizeof(cplx) + sizeof(int));
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_invert, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((size_t)kMaxInvert * (2 * sizeof(cplx) + sizeof(int))));
+    attr_set = true;
+  }
+  dim3 grid(nops, nE);
+  k_invert<<<grid, kInvThreads, smem, st>>>(ops, status, e_base);
+}
+
+void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,
+                 cudaStream_t st) {
+  if (ntiles == 0) return;
+  dim3 grid(ntiles, nE);
+  if (big)
+    k_zgemm<64, 64, 8><<<grid, 256, 0, st>>>(ops, tile_op);
+  else
+    k_zgemm<32, 32, 8><<<grid, 64, 0, st>>>(ops, tile_op);
+}
+
+void launch_extract(const ExtractOp* ops, int nops, const LeafBond* bonds, const DevProblem& P,
+                    int lesser, int want_bonds, cplx* diagG, cplx* diagGl, double* J,
+                    int64_t n_nodes, int64_t n_bonds, int nE, cudaStream_t st) {
+  if (nops == 0) return;
+  dim3 grid(nops, nE);
+  k_extract<<<grid, 256, 0, st>>>(ops, bonds, P, lesser, want_bonds, diagG, diagGl, J, n_nodes,
+                                  n_bonds);
+}
+
+}  // namespace findgb

@@ -1,0 +1,87 @@
+// Descriptors shared by the host runtime and the CUDA kernels of the FIND
+// passes, and the launch wrappers.  All complex data are interleaved double
+// pairs (double2: x = re, y = im).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "plan.hpp"  // Pos, LeafBond
+
+namespace findgb {
+
+typedef double2 cplx;
+
+// Per-call constants of the mesh problem A = E I - H - Sigma_L - Sigma_R.
+struct DevProblem {
+  int nx, ny, stencil;
+  double t, tp, onsite0;
+  const double* V;         // n onsite disorder values
+  const cplx* E;           // energies of the current pass
+  const cplx* sigL;        // [e][nx][nx]
+  const cplx* sigR;        // [e][nx][nx]
+  double fL, fR;
+  const cplx* dles;        // node-diagonal Sigma< or nullptr
+  int64_t dles_estride;    // 0 when shared by all energies
+};
+
+// Assembly of one op: M (and Sigma_M) over n positions, one CTA per row.
+struct AsmOp {
+  int n, row0;
+  int64_t pos;
+  const cplx* u1; const cplx* r1; int d1;  // source 1 (energy 0), stride d1*d1
+  const cplx* u2; const cplx* r2; int d2;  // source 2
+  cplx* M;                                 // energy 0; S_M = M + n*n
+  int64_t estride;                         // per-energy stride of the op scratch
+};
+
+// In-place Gauss-Jordan inversion of the leading s x s block of M (ld).
+struct InvOp {
+  cplx* M;
+  int64_t estride;
+  int ld, s;
+};
+
+// D = beta * C + alpha * A op(B) + alpha2 * A2 op(B2); op(B) = B (opb 0) or
+// B^H (opb 1, B stored n x k).  Every operand is row-major with its leading
+// dimension and a per-energy stride.
+struct GemmOp {
+  int m, n, k, k2;
+  const cplx* A; int lda; int64_t sa;
+  const cplx* B; int ldb; int64_t sb; int opb;
+  const cplx* A2; int lda2; int64_t sa2;
+  const cplx* B2; int ldb2; int64_t sb2; int opb2;
+  const cplx* C; int ldc; int64_t sc;
+  cplx* D; int ldd; int64_t sd;
+  double alpha, alpha2, beta;
+  int tile0, tiles_n;
+};
+
+struct ExtractOp {
+  const cplx* K;       // inverted bordered system G_K (energy 0), n x n
+  const cplx* Q;       // rows C of G<_K (energy 0), c x n
+  int64_t estride;
+  int n, nb, c;
+  int x0, y0, wx;
+  int64_t bond;
+  int nbond;
+};
+
+// ---- launch wrappers (kernels.cu)
+void launch_lead_modes(const cplx* E, int nE, const double* eps, const double* tau, int nx,
+                       cplx* sig_modes, cudaStream_t st);
+void launch_lead_dense(const cplx* sig_modes, const double* phi, int nx, int nE, cplx* out,
+                       cudaStream_t st);
+void launch_assemble(const AsmOp* ops, const int* row_op, int nrows, const Pos* pos,
+                     const DevProblem& P, int lesser, int nE, cudaStream_t st);
+void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
+                   cudaStream_t st);
+void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,
+                 cudaStream_t st);
+void launch_extract(const ExtractOp* ops, int nops, const LeafBond* bonds, const DevProblem& P,
+                    int lesser, int want_bonds, cplx* diagG, cplx* diagGl, double* J,
+                    int64_t n_nodes, int64_t n_bonds, int nE, cudaStream_t st);
+
+constexpr int kMaxInvert = 2048;  // largest block the in-CTA inversion accepts
+
+}  // namespace findgb

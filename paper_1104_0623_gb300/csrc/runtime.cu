@@ -1,0 +1,744 @@
+// C ABI of the FIND library: handle, device workspace, per-level descriptor
+// tables and the launch sequence of one solve.
+//
+// Execution of one pass over a batch of energies (all on the caller's stream):
+//   lead self-energies (closed form, unless given)
+//   upward levels by height:   assemble -> invert M(S,S) -> L -> U (+T) (-> R)
+//   downward levels by depth:  the same kernels on the complement clusters
+//   leaf level:                assemble K -> invert K -> (G_K Sigma_K, .. G_K^H)
+//                              -> extract diag G, diag G<, bond currents
+// U and R of every cluster stay resident in one workspace allocation laid out
+// [matrix id][energy][b][b]; per-level scratch holds M, Sigma_M, L, T.
+#include "../../include/find.h"
+#include "kernels.cuh"
+#include "plan.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using findgb::cplx;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+bool device_accessible(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Byte arena used twice: once to size the descriptor tables, once to fill them.
+struct Arena {
+  std::vector<unsigned char> buf;
+  template <class T>
+  size_t put(const std::vector<T>& v) {
+    size_t off = (buf.size() + 255) & ~size_t(255);
+    buf.resize(off + v.size() * sizeof(T));
+    if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+  }
+};
+
+struct Stage {
+  size_t ops = 0, small = 0, big = 0;  // arena offsets
+  int nsmall = 0, nbig = 0;
+};
+
+struct Level {
+  bool leaf = false;
+  int nops = 0, nrows = 0, max_s = 0;
+  size_t asmops = 0, row_op = 0, inv = 0, ext = 0;  // arena offsets
+  Stage st[3];
+  int nstages = 0;
+};
+
+struct Layout {  // byte offsets inside the workspace
+  size_t V, phi, eps, tau, E, sigL, sigR, modes, dles, U, R, scratch, oG, oGl, oJ, pos, bonds,
+      status, meta, total;
+};
+
+}  // namespace
+
+struct find_handle {
+  findgb::Plan plan;
+  find_desc desc{};
+  std::vector<double> V, phi, eps, tau;
+  std::string err;
+  // current workspace
+  int batch = 0, lesser = -1;
+  unsigned char* ws = nullptr;
+  Layout lay{};
+  std::vector<Level> levels;  // upward, then downward, then the leaf level
+  int n_up = 0, n_dn = 0;
+};
+
+namespace {
+
+int fail(find_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(find_handle* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return fail(h, e == cudaErrorMemoryAllocation ? FIND_ENOMEM : FIND_ECUDA, m);
+}
+
+int64_t op_slot_elems(const findgb::ElimOp& op, bool lesser) {
+  int64_t n = op.n, bs = (int64_t)op.b * op.s;
+  return lesser ? 2 * n * n + 2 * bs : n * n + bs;
+}
+
+int64_t leaf_slot_elems(const findgb::LeafOp& op, bool lesser) {
+  int64_t n = op.n;
+  return lesser ? 2 * n * n + 2 * (int64_t)op.c * n : n * n;
+}
+
+// Adds one GEMM op to a stage, assigning its tiles to the small or big class.
+void add_gemm(findgb::GemmOp g, std::vector<findgb::GemmOp>& ops, std::vector<int>& small,
+              std::vector<int>& big) {
+  if (g.m == 0 || g.n == 0) return;
+  bool is_big = std::max(g.m, g.n) > 32;
+  int bm = is_big ? 64 : 32;
+  int tm = (g.m + bm - 1) / bm, tn = (g.n + bm - 1) / bm;
+  std::vector<int>& map = is_big ? big : small;
+  g.tile0 = (int)map.size();
+  g.tiles_n = tn;
+  int id = (int)ops.size();
+  ops.push_back(g);
+  for (int t = 0; t < tm * tn; ++t) map.push_back(id);
+}
+
+findgb::GemmOp gemm0() {
+  findgb::GemmOp g;
+  std::memset(&g, 0, sizeof(g));
+  g.alpha = 1.0;
+  g.alpha2 = 1.0;
+  return g;
+}
+
+// Host-side bounds check of every operand a kernel will touch: each row-major
+// block (rows x cols, leading dimension ld, per-energy stride) must lie inside
+// [lo, hi) for all `batch` energies.  Run on the real tables before upload.
+struct Bounds {
+  const unsigned char* lo = nullptr;
+  const unsigned char* hi = nullptr;
+  std::string err;
+  void block(const cplx* p, int64_t rows, int64_t cols, int64_t ld, int64_t estride, int batch,
+             const char* what) {
+    if (!err.empty() || !lo || rows <= 0 || cols <= 0) return;
+    if (!p || ld < cols) { err = std::string(what) + ": null pointer or ld < cols"; return; }
+    const unsigned char* first = reinterpret_cast<const unsigned char*>(p);
+    const unsigned char* last = reinterpret_cast<const unsigned char*>(
+        p + (rows - 1) * ld + cols + (int64_t)(batch - 1) * estride);
+    if (first < lo || last > hi) err = std::string(what) + ": operand outside the workspace";
+  }
+};
+
+// Builds every level's descriptor tables into `ar`, with device pointers
+// computed from `base` (the workspace address; 0 for sizing).
+void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batch, bool lesser,
+                  Arena& ar, std::vector<Level>& levels, int64_t& scratch_elems, Bounds* bc = nullptr) {
+  const findgb::Plan& p = h->plan;
+  cplx* U = reinterpret_cast<cplx*>(base + L.U);
+  cplx* R = lesser ? reinterpret_cast<cplx*>(base + L.R) : nullptr;
+  cplx* S0 = reinterpret_cast<cplx*>(base + L.scratch);
+  auto umat = [&](int id) { return id < 0 ? (cplx*)nullptr : U + p.mat_off[id] * batch; };
+  auto rmat = [&](int id) { return (id < 0 || !R) ? (cplx*)nullptr : R + p.mat_off[id] * batch; };
+  levels.clear();
+  scratch_elems = 0;
+  auto gemm_ok = [&](const findgb::GemmOp& q) {
+    if (!bc || q.m == 0 || q.n == 0) return;
+    bc->block(q.A, q.m, q.k, q.lda, q.sa, batch, "gemm A");
+    if (q.opb == 0) bc->block(q.B, q.k, q.n, q.ldb, q.sb, batch, "gemm B");
+    else bc->block(q.B, q.n, q.k, q.ldb, q.sb, batch, "gemm B^H");
+    if (q.A2) {
+      bc->block(q.A2, q.m, q.k2, q.lda2, q.sa2, batch, "gemm A2");
+      if (q.opb2 == 0) bc->block(q.B2, q.k2, q.n, q.ldb2, q.sb2, batch, "gemm B2");
+      else bc->block(q.B2, q.n, q.k2, q.ldb2, q.sb2, batch, "gemm B2^H");
+    }
+    if (q.C) bc->block(q.C, q.m, q.n, q.ldc, q.sc, batch, "gemm C");
+    bc->block(q.D, q.m, q.n, q.ldd, q.sd, batch, "gemm D");
+  };
+
+  auto elim_level = [&](const std::vector<findgb::ElimOp>& ops) {
+    Level lv;
+    std::vector<findgb::AsmOp> asmops;
+    std::vector<int> row_op;
+    std::vector<findgb::InvOp> inv;
+    std::vector<findgb::GemmOp> g[3];
+    std::vector<int> sm[3], bg[3];
+    int64_t off = 0;
+    for (const auto& op : ops) {
+      const int64_t slot = op_slot_elems(op, lesser);
+      cplx* M = S0 + off * batch;
+      cplx* Sg = M + (int64_t)op.n * op.n;
+      cplx* Lm = M + (lesser ? 2 : 1) * (int64_t)op.n * op.n;
+      cplx* T = Lm + (int64_t)op.b * op.s;
+      off += slot;
+      const int n = op.n, s = op.s, b = op.b;
+      findgb::AsmOp a;
+      a.n = n;
+      a.row0 = lv.nrows;
+      a.pos = op.pos;
+      a.u1 = umat(op.src1); a.r1 = rmat(op.src1); a.d1 = op.src1 < 0 ? 0 : p.mat_dim[op.src1];
+      a.u2 = umat(op.src2); a.r2 = rmat(op.src2); a.d2 = op.src2 < 0 ? 0 : p.mat_dim[op.src2];
+      a.M = M;
+      a.estride = slot;
+      for (int r = 0; r < n; ++r) row_op.push_back((int)asmops.size());
+      lv.nrows += n;
+      asmops.push_back(a);
+      if (bc) {
+        bc->block(M, lesser ? 2 * (int64_t)n : n, n, n, slot, batch, "assemble M");
+        if (a.u1) bc->block(a.u1, a.d1, a.d1, a.d1, (int64_t)a.d1 * a.d1, batch, "source U1");
+        if (a.u2) bc->block(a.u2, a.d2, a.d2, a.d2, (int64_t)a.d2 * a.d2, batch, "source U2");
+        if (a.r1) bc->block(a.r1, a.d1, a.d1, a.d1, (int64_t)a.d1 * a.d1, batch, "source R1");
+        if (a.r2) bc->block(a.r2, a.d2, a.d2, a.d2, (int64_t)a.d2 * a.d2, batch, "source R2");
+        for (int q = 0; q < n && bc->err.empty(); ++q) {
+          const findgb::Pos& pq = p.pos[op.pos + q];
+          int d = pq.src == 1 ? a.d1 : pq.src == 2 ? a.d2 : 1;
+          if (pq.idx < 0 || pq.idx >= d || pq.node < 0 || pq.node >= p.nx * p.ny)
+            bc->err = "assemble: gather index out of range";
+        }
+      }
+      inv.push_back(findgb::InvOp{M, slot, n, s});
+      lv.max_s = std::max(lv.max_s, s);
+      // stage 0: L = M(B,S) X, X = M(S,S)^{-1} in place   (Eq. 13)
+      findgb::GemmOp q = gemm0();
+      q.m = b; q.n = s; q.k = s;
+      q.A = M + (int64_t)s * n; q.lda = n; q.sa = slot;
+      q.B = M; q.ldb = n; q.sb = slot;
+      q.D = Lm; q.ldd = s; q.sd = slot;
+      gemm_ok(q); add_gemm(q, g[0], sm[0], bg[0]);
+      // stage 1: U = M(B,B) - L M(S,B)                        (Eq. 2)
+      q = gemm0();
+      q.m = b; q.n = b; q.k = s;
+      q.A = Lm; q.lda = s; q.sa = slot; q.alpha = -1.0;
+      q.B = M + s; q.ldb = n; q.sb = slot;
+      q.C = M + (int64_t)s * n + s; q.ldc = n; q.sc = slot; q.beta = 1.0;
+      q.D = umat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
+      gemm_ok(q); add_gemm(q, g[1], sm[1], bg[1]);
+      if (lesser) {
+        // stage 1: T = L Sigma(S,S) - Sigma(B,S)
+        q = gemm0();
+        q.m = b; q.n = s; q.k = s;
+        q.A = Lm; q.lda = s; q.sa = slot;
+        q.B = Sg; q.ldb = n; q.sb = slot;
+        q.C = Sg + (int64_t)s * n; q.ldc = n; q.sc = slot; q.beta = -1.0;
+        q.D = T; q.ldd = s; q.sd = slot;
+        gemm_ok(q); add_gemm(q, g[1], sm[1], bg[1]);
+        // stage 2: R = Sigma(B,B) - L Sigma(S,B) + T L^H     (Eq. 7)
+        q = gemm0();
+        q.m = b; q.n = b; q.k = s; q.k2 = s;
+        q.A = Lm; q.lda = s; q.sa = slot; q.alpha = -1.0;
+        q.B = Sg + s; q.ldb = n; q.sb = slot;
+        q.A2 = T; q.lda2 = s; q.sa2 = slot; q.alpha2 = 1.0;
+        q.B2 = Lm; q.ldb2 = s; q.sb2 = slot; q.opb2 = 1;
+        q.C = Sg + (int64_t)s * n + s; q.ldc = n; q.sc = slot; q.beta = 1.0;
+        q.D = rmat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
+        gemm_ok(q); add_gemm(q, g[2], sm[2], bg[2]);
+      }
+    }
+    lv.nops = (int)ops.size();
+    lv.asmops = ar.put(asmops);
+    lv.row_op = ar.put(row_op);
+    lv.inv = ar.put(inv);
+    lv.nstages = lesser ? 3 : 2;
+    for (int k = 0; k < lv.nstages; ++k) {
+      lv.st[k].ops = ar.put(g[k]);
+      lv.st[k].small = ar.put(sm[k]);
+      lv.st[k].big = ar.put(bg[k]);
+      lv.st[k].nsmall = (int)sm[k].size();
+      lv.st[k].nbig = (int)bg[k].size();
+    }
+    scratch_elems = std::max(scratch_elems, off);
+    levels.push_back(lv);
+  };
+
+  for (const auto& lv : p.up_levels) elim_level(lv);
+  h->n_up = (int)p.up_levels.size();
+  for (const auto& lv : p.dn_levels) elim_level(lv);
+  h->n_dn = (int)p.dn_levels.size();
+
+  // leaf level
+  {
+    Level lv;
+    lv.leaf = true;
+    std::vector<findgb::AsmOp> asmops;
+    std::vector<int> row_op;
+    std::vector<findgb::InvOp> inv;
+    std::vector<findgb::GemmOp> g[2];
+    std::vector<int> sm[2], bg[2];
+    std::vector<findgb::ExtractOp> ext;
+    int64_t off = 0;
+    for (const auto& op : p.leaf_ops) {
+      const int64_t slot = leaf_slot_elems(op, lesser);
+      cplx* M = S0 + off * batch;
+      cplx* Sg = M + (int64_t)op.n * op.n;
+      cplx* P = M + 2 * (int64_t)op.n * op.n;
+      cplx* Q = P + (int64_t)op.c * op.n;
+      off += slot;
+      const int n = op.n;
+      findgb::AsmOp a;
+      a.n = n;
+      a.row0 = lv.nrows;
+      a.pos = op.pos;
+      a.u1 = umat(op.src); a.r1 = rmat(op.src); a.d1 = op.src < 0 ? 0 : p.mat_dim[op.src];
+      a.u2 = nullptr; a.r2 = nullptr; a.d2 = 0;
+      a.M = M;
+      a.estride = slot;
+      for (int r = 0; r < n; ++r) row_op.push_back((int)asmops.size());
+      lv.nrows += n;
+      asmops.push_back(a);
+      if (bc) {
+        bc->block(M, lesser ? 2 * (int64_t)n + 2 * op.c : n, n, n, slot, batch, "leaf scratch");
+        if (a.u1) bc->block(a.u1, a.d1, a.d1, a.d1, (int64_t)a.d1 * a.d1, batch, "leaf U");
+        if (a.r1) bc->block(a.r1, a.d1, a.d1, a.d1, (int64_t)a.d1 * a.d1, batch, "leaf R");
+        for (int q = 0; q < n && bc->err.empty(); ++q) {
+          const findgb::Pos& pq = p.pos[op.pos + q];
+          int d = pq.src == 1 ? a.d1 : 1;
+          if (pq.src == 2 || pq.idx < 0 || pq.idx >= d || pq.node < 0 || pq.node >= p.nx * p.ny)
+            bc->err = "leaf assemble: gather index out of range";
+        }
+        for (int b = 0; b < op.nbond && bc->err.empty(); ++b) {
+          const findgb::LeafBond& lb = p.bonds[op.bond + b];
+          if (lb.pi < op.nb || lb.pi >= n || lb.pj < 0 || lb.pj >= n || lb.bond < 0 || lb.bond >= p.n_bonds)
+            bc->err = "leaf bond index out of range";
+        }
+      }
+      inv.push_back(findgb::InvOp{M, slot, n, n});
+      lv.max_s = std::max(lv.max_s, n);
+      if (lesser) {
+        // P = G_K(C, :) Sigma_K
+        findgb::GemmOp q = gemm0();
+        q.m = op.c; q.n = n; q.k = n;
+        q.A = M + (int64_t)op.nb * n; q.lda = n; q.sa = slot;
+        q.B = Sg; q.ldb = n; q.sb = slot;
+        q.D = P; q.ldd = n; q.sd = slot;
+        gemm_ok(q); add_gemm(q, g[0], sm[0], bg[0]);
+        // Q = P G_K^H = G<_K(C, :)
+        q = gemm0();
+        q.m = op.c; q.n = n; q.k = n;
+        q.A = P; q.lda = n; q.sa = slot;
+        q.B = M; q.ldb = n; q.sb = slot; q.opb = 1;
+        q.D = Q; q.ldd = n; q.sd = slot;
+        gemm_ok(q); add_gemm(q, g[1], sm[1], bg[1]);
+      }
+      findgb::ExtractOp x;
+      x.K = M;
+      x.Q = lesser ? Q : nullptr;
+      x.estride = slot;
+      x.n = n; x.nb = op.nb; x.c = op.c;
+      x.x0 = op.x0; x.y0 = op.y0; x.wx = op.wx;
+      x.bond = op.bond; x.nbond = op.nbond;
+      ext.push_back(x);
+    }
+    lv.nops = (int)p.leaf_ops.size();
+    lv.asmops = ar.put(asmops);
+    lv.row_op = ar.put(row_op);
+    lv.inv = ar.put(inv);
+    lv.ext = ar.put(ext);
+    lv.nstages = lesser ? 2 : 0;
+    for (int k = 0; k < lv.nstages; ++k) {
+      lv.st[k].ops = ar.put(g[k]);
+      lv.st[k].small = ar.put(sm[k]);
+      lv.st[k].big = ar.put(bg[k]);
+      lv.st[k].nsmall = (int)sm[k].size();
+      lv.st[k].nbig = (int)bg[k].size();
+    }
+    scratch_elems = std::max(scratch_elems, off);
+    levels.push_back(lv);
+  }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Computes the workspace layout for (batch, lesser); meta_bytes is the size
+// of the descriptor arena.
+Layout make_layout(const find_handle* h, int batch, bool lesser, int64_t scratch_elems,
+                   size_t meta_bytes) {
+  const findgb::Plan& p = h->plan;
+  const size_t n = (size_t)p.nx * p.ny, nx = p.nx, c16 = sizeof(cplx);
+  Layout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
+  L.V = take(n * 8);
+  L.phi = take(nx * nx * 8);
+  L.eps = take(nx * 8);
+  L.tau = take(nx * 8);
+  L.E = take(batch * c16);
+  L.sigL = take(batch * nx * nx * c16);
+  L.sigR = take(batch * nx * nx * c16);
+  L.modes = take(batch * nx * c16);
+  L.dles = take(lesser ? batch * n * c16 : 0);
+  L.U = take((size_t)p.mat_elems * batch * c16);
+  L.R = take(lesser ? (size_t)p.mat_elems * batch * c16 : 0);
+  L.scratch = take((size_t)scratch_elems * batch * c16);
+  L.oG = take(batch * n * c16);
+  L.oGl = take(lesser ? batch * n * c16 : 0);
+  L.oJ = take(lesser ? batch * (size_t)p.n_bonds * 8 : 0);
+  L.pos = take(p.pos.size() * sizeof(findgb::Pos));
+  L.bonds = take(p.bonds.size() * sizeof(findgb::LeafBond));
+  L.status = take(256);
+  L.meta = take(meta_bytes);
+  L.total = o;
+  return L;
+}
+
+double workspace_bytes(find_handle* h, int batch, bool lesser, std::string* check_err = nullptr) {
+  Arena ar;
+  std::vector<Level> lv;
+  int64_t se = 0;
+  Layout L0 = make_layout(h, batch, lesser, 0, 0);
+  build_tables(h, nullptr, L0, batch, lesser, ar, lv, se);
+  Layout L = make_layout(h, batch, lesser, se, ar.buf.size());
+  if (check_err) {
+    // the same bounds check as before an upload, against a synthetic base
+    // address (nothing is dereferenced)
+    unsigned char* fake = reinterpret_cast<unsigned char*>(uintptr_t(1) << 40);
+    Arena a2;
+    Bounds bc;
+    bc.lo = fake;
+    bc.hi = fake + L.meta;
+    build_tables(h, fake, L, batch, lesser, a2, lv, se, &bc);
+    *check_err = bc.err;
+  }
+  return (double)L.total;
+}
+
+void release(find_handle* h) {
+  if (h->ws) cudaFree(h->ws);
+  h->ws = nullptr;
+  h->batch = 0;
+  h->lesser = -1;
+  h->levels.clear();
+}
+
+int ensure_workspace(find_handle* h, int batch, bool lesser) {
+  if (h->ws && h->batch >= batch && (h->lesser == 1 || !lesser)) return FIND_OK;
+  release(h);
+  Arena ar;
+  std::vector<Level> lv;
+  int64_t se = 0;
+  Layout L0 = make_layout(h, batch, lesser, 0, 0);
+  build_tables(h, nullptr, L0, batch, lesser, ar, lv, se);
+  Layout L = make_layout(h, batch, lesser, se, ar.buf.size());
+  unsigned char* ws = nullptr;
+  cudaError_t e = cudaMalloc(&ws, L.total);
+  if (e != cudaSuccess) return cuda_fail(h, e, "workspace allocation");
+  h->ws = ws;
+  h->lay = L;
+  h->batch = batch;
+  h->lesser = lesser ? 1 : 0;
+  Arena real;
+  Bounds bc;
+  bc.lo = ws;
+  bc.hi = ws + L.meta;
+  build_tables(h, ws, L, batch, lesser, real, h->levels, se, &bc);
+  if (!bc.err.empty()) {
+    release(h);
+    return fail(h, FIND_EINVAL, "internal table check failed: " + bc.err);
+  }
+  const findgb::Plan& p = h->plan;
+  e = cudaMemcpy(ws + L.V, h->V.data(), h->V.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ws + L.phi, h->phi.data(), h->phi.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ws + L.eps, h->eps.data(), h->eps.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ws + L.tau, h->tau.data(), h->tau.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ws + L.pos, p.pos.data(), p.pos.size() * sizeof(findgb::Pos), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !p.bonds.empty())
+    e = cudaMemcpy(ws + L.bonds, p.bonds.data(), p.bonds.size() * sizeof(findgb::LeafBond),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ws + L.meta, real.buf.data(), real.buf.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    release(h);
+    return cuda_fail(h, e, "workspace upload");
+  }
+  return FIND_OK;
+}
+
+int choose_batch(find_handle* h, int nE, bool lesser) {
+  if (h->desc.max_batch > 0) return std::min(h->desc.max_batch, nE);
+  size_t fr = 0, tot = 0;
+  if (h->ws && h->lesser >= (lesser ? 1 : 0)) return std::min(h->batch, nE);
+  cudaMemGetInfo(&fr, &tot);
+  double one = workspace_bytes(h, 1, lesser);
+  double two = workspace_bytes(h, 2, lesser);
+  double per = std::max(1.0, two - one);
+  double budget = 0.70 * (double)fr - (one - per);
+  int b = (int)std::floor(budget / per);
+  return std::max(1, std::min({b, 64, nE}));
+}
+
+template <class T>
+const T* at(const find_handle* h, size_t off) {
+  return reinterpret_cast<const T*>(h->ws + h->lay.meta + off);
+}
+
+void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, bool lesser,
+               int e_base, int nb, cudaStream_t st, cplx* oG, cplx* oGl, double* oJ,
+               int want_bonds) {
+  const Layout& L = h->lay;
+  auto pos = reinterpret_cast<const findgb::Pos*>(h->ws + L.pos);
+  int* status = reinterpret_cast<int*>(h->ws + L.status);
+  findgb::launch_assemble(at<findgb::AsmOp>(h, lv.asmops), at<int>(h, lv.row_op), lv.nrows, pos, P,
+                          lesser ? 1 : 0, nb, st);
+  findgb::launch_invert(at<findgb::InvOp>(h, lv.inv), lv.nops, lv.max_s, status, e_base, nb, st);
+  for (int k = 0; k < lv.nstages; ++k) {
+    const Stage& s = lv.st[k];
+    const findgb::GemmOp* ops = at<findgb::GemmOp>(h, s.ops);
+    findgb::launch_gemm(ops, at<int>(h, s.small), s.nsmall, 0, nb, st);
+    findgb::launch_gemm(ops, at<int>(h, s.big), s.nbig, 1, nb, st);
+  }
+  if (lv.leaf)
+    findgb::launch_extract(at<findgb::ExtractOp>(h, lv.ext), lv.nops,
+                           reinterpret_cast<const findgb::LeafBond*>(h->ws + L.bonds), P,
+                           lesser ? 1 : 0, want_bonds, oG, oGl, oJ,
+                           (int64_t)h->plan.nx * h->plan.ny, h->plan.n_bonds, nb, st);
+}
+
+int solve(find_handle* h, const double* E, int nE, const double* sigL, const double* sigR,
+          double fL, double fR, const double* dles, int dles_per_e, double* G, double* Gl,
+          double* J, void* stream, bool lesser) {
+  if (!h) return fail(nullptr, FIND_EINVAL, "null handle");
+  if (nE < 0) return fail(h, FIND_EINVAL, "nE < 0");
+  if (nE == 0) return FIND_OK;
+  if (!E || !G || (lesser && !Gl)) return fail(h, FIND_EINVAL, "E and the diag outputs must not be NULL");
+  DeviceGuard guard(h->desc.device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const findgb::Plan& p = h->plan;
+  const int64_t n = (int64_t)p.nx * p.ny, nx = p.nx;
+  int batch = choose_batch(h, nE, lesser);
+  int rc = ensure_workspace(h, batch, lesser);
+  if (rc != FIND_OK) return rc;
+  batch = std::min(batch, h->batch);
+  const Layout& L = h->lay;
+  unsigned char* ws = h->ws;
+  cplx* dE = reinterpret_cast<cplx*>(ws + L.E);
+  cplx* dsL = reinterpret_cast<cplx*>(ws + L.sigL);
+  cplx* dsR = reinterpret_cast<cplx*>(ws + L.sigR);
+  cplx* dmodes = reinterpret_cast<cplx*>(ws + L.modes);
+  cplx* ddl = reinterpret_cast<cplx*>(ws + L.dles);
+  int* status = reinterpret_cast<int*>(ws + L.status);
+  const bool dG = device_accessible(G);
+  const bool dGl = !lesser || device_accessible(Gl);
+  const bool dJ = !lesser || !J || device_accessible(J);
+  const int want_bonds = (lesser && J) ? 1 : 0;
+
+  cudaError_t e = cudaMemsetAsync(status, 0x7f, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
+  const int kNoError = 0x7f7f7f7f;
+  if (lesser && dles && !dles_per_e) {
+    e = cudaMemcpyAsync(ddl, dles, n * sizeof(cplx), cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sigma_lesser_diag copy");
+  }
+  for (int e0 = 0; e0 < nE; e0 += batch) {
+    const int nb = std::min(batch, nE - e0);
+    e = cudaMemcpyAsync(dE, E + 2 * (int64_t)e0, nb * sizeof(cplx), cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "energy copy");
+    const cplx* useL = dsL;
+    const cplx* useR = dsR;
+    if (!sigL || !sigR) {
+      findgb::launch_lead_modes(dE, nb, reinterpret_cast<const double*>(ws + L.eps),
+                                reinterpret_cast<const double*>(ws + L.tau), (int)nx, dmodes, st);
+      cplx* dst = !sigL ? dsL : dsR;
+      findgb::launch_lead_dense(dmodes, reinterpret_cast<const double*>(ws + L.phi), (int)nx, nb,
+                                dst, st);
+      if (!sigL && !sigR) useR = dsL;
+    }
+    if (sigL) {
+      e = cudaMemcpyAsync(dsL, sigL + 2 * (int64_t)e0 * nx * nx, nb * nx * nx * sizeof(cplx),
+                          cudaMemcpyDefault, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "sigmaL copy");
+      if (!sigR) useR = dsR;
+    }
+    if (sigR) {
+      e = cudaMemcpyAsync(dsR, sigR + 2 * (int64_t)e0 * nx * nx, nb * nx * nx * sizeof(cplx),
+                          cudaMemcpyDefault, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "sigmaR copy");
+    }
+    if (!sigL && sigR) useL = dsL;
+    findgb::DevProblem P;
+    P.nx = p.nx; P.ny = p.ny; P.stencil = p.stencil;
+    P.t = h->desc.t; P.tp = h->desc.tp; P.onsite0 = h->desc.onsite0;
+    P.V = reinterpret_cast<const double*>(ws + L.V);
+    P.E = dE; P.sigL = useL; P.sigR = useR;
+    P.fL = fL; P.fR = fR;
+    P.dles = nullptr; P.dles_estride = 0;
+    if (lesser && dles) {
+      P.dles = ddl;
+      if (dles_per_e) {
+        P.dles_estride = n;
+        e = cudaMemcpyAsync(ddl, dles + 2 * (int64_t)e0 * n, nb * n * sizeof(cplx), cudaMemcpyDefault, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "sigma_lesser_diag copy");
+      }
+    }
+    cplx* oG = dG ? reinterpret_cast<cplx*>(G) + (int64_t)e0 * n : reinterpret_cast<cplx*>(ws + L.oG);
+    cplx* oGl = lesser ? (dGl ? reinterpret_cast<cplx*>(Gl) + (int64_t)e0 * n
+                              : reinterpret_cast<cplx*>(ws + L.oGl))
+                       : nullptr;
+    double* oJ = want_bonds ? (dJ ? J + (int64_t)e0 * p.n_bonds : reinterpret_cast<double*>(ws + L.oJ))
+                            : nullptr;
+    for (const Level& lv : h->levels) run_level(h, lv, P, lesser, e0, nb, st, oG, oGl, oJ, want_bonds);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+    if (!dG) {
+      e = cudaMemcpyAsync(G + 2 * (int64_t)e0 * n, oG, nb * n * sizeof(cplx), cudaMemcpyDefault, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "diagG copy-out");
+    }
+    if (lesser && !dGl) {
+      e = cudaMemcpyAsync(Gl + 2 * (int64_t)e0 * n, oGl, nb * n * sizeof(cplx), cudaMemcpyDefault, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "diagGl copy-out");
+    }
+    if (want_bonds && !dJ) {
+      e = cudaMemcpyAsync(J + (int64_t)e0 * p.n_bonds, oJ, nb * (size_t)p.n_bonds * 8, cudaMemcpyDefault, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "bond current copy-out");
+    }
+  }
+  int hs = kNoError;
+  e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "solve");
+  if (hs != kNoError) {
+    char buf[128];
+    std::snprintf(buf, sizeof buf, "exactly zero pivot at energy index %d", hs);
+    return fail(h, FIND_ESINGULAR, buf);
+  }
+  h->err.clear();
+  return FIND_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int find_create(const find_desc* d, find_handle** out) {
+  if (!d || !out) return fail(nullptr, FIND_EINVAL, "null descriptor or output");
+  *out = nullptr;
+  if (d->precision != FIND_FP64) return fail(nullptr, FIND_EINVAL, "only FIND_FP64 is supported");
+  if (d->stencil != 5 && d->stencil != 9) return fail(nullptr, FIND_EINVAL, "stencil must be 5 or 9");
+  if (d->max_batch < 0) return fail(nullptr, FIND_EINVAL, "max_batch < 0");
+  find_handle* h = new (std::nothrow) find_handle();
+  if (!h) return fail(nullptr, FIND_ENOMEM, "host allocation");
+  h->desc = *d;
+  h->desc.onsite_V = nullptr;
+  if (h->desc.leaf <= 0) h->desc.leaf = 8;
+  std::string err;
+  if (findgb::build_plan(d->nx, d->ny, d->stencil, h->desc.leaf, h->plan, err) != 0) {
+    delete h;
+    return fail(nullptr, FIND_EINVAL, err);
+  }
+  if (std::max(h->plan.max_s, h->plan.max_kn) > findgb::kMaxInvert) {
+    delete h;
+    return fail(nullptr, FIND_EINVAL, "a private-inner or bordered leaf set exceeds 2048 nodes");
+  }
+  const size_t n = (size_t)d->nx * d->ny;
+  h->V.assign(n, 0.0);
+  if (d->onsite_V) {
+    if (device_accessible(d->onsite_V)) {
+      cudaError_t e = cudaMemcpy(h->V.data(), d->onsite_V, n * 8, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        delete h;
+        return fail(nullptr, FIND_ECUDA, std::string("onsite_V copy: ") + cudaGetErrorString(e));
+      }
+    } else {
+      std::memcpy(h->V.data(), d->onsite_V, n * 8);
+    }
+  }
+  // transverse sine modes of the leads: phi[x][m], eps_m, tau_m
+  const int nx = d->nx;
+  h->phi.resize((size_t)nx * nx);
+  h->eps.resize(nx);
+  h->tau.resize(nx);
+  const double pi = 3.14159265358979323846;
+  for (int m = 1; m <= nx; ++m) {
+    double th = m * pi / (nx + 1);
+    h->eps[m - 1] = d->onsite0 - 2.0 * d->t * std::cos(th);
+    h->tau[m - 1] = (d->stencil == 9) ? -d->t - 2.0 * d->tp * std::cos(th) : -d->t;
+    for (int x = 0; x < nx; ++x)
+      h->phi[(size_t)x * nx + (m - 1)] = std::sqrt(2.0 / (nx + 1)) * std::sin(m * (x + 1) * pi / (nx + 1));
+  }
+  *out = h;
+  return FIND_OK;
+}
+
+int find_plan_info(const find_handle* h, find_plan_stats* o) {
+  if (!h || !o) return FIND_EINVAL;
+  const findgb::Plan& p = h->plan;
+  o->n_clusters = (int)p.cl.size();
+  o->n_leaves = p.n_leaves;
+  o->n_up_levels = (int)p.up_levels.size();
+  o->n_down_levels = (int)p.dn_levels.size();
+  o->max_s = p.max_s;
+  o->max_b = p.max_b;
+  o->max_kn = p.max_kn;
+  o->n_bonds = p.n_bonds;
+  o->flops_diag = p.flops_diag;
+  o->flops_lesser = p.flops_lesser;
+  o->ur_bytes = 2.0 * (double)p.mat_elems * sizeof(cplx);
+  find_handle* hh = const_cast<find_handle*>(h);
+  o->scratch_bytes = workspace_bytes(hh, 2, true) - workspace_bytes(hh, 1, true) - o->ur_bytes -
+                     (double)(3 * (size_t)p.nx * p.ny * 16 + 2 * (size_t)p.nx * p.nx * 16);
+  return FIND_OK;
+}
+
+int find_workspace_bytes(const find_handle* h, int batch, int lesser, double* bytes) {
+  if (!h || !bytes || batch < 1) return FIND_EINVAL;
+  find_handle* hh = const_cast<find_handle*>(h);
+  std::string err;
+  *bytes = workspace_bytes(hh, batch, lesser != 0, &err);
+  if (!err.empty()) return fail(hh, FIND_EINVAL, "internal table check failed: " + err);
+  return FIND_OK;
+}
+
+int find_solve_diag(find_handle* h, const double* E, int nE, const double* sigmaL,
+                    const double* sigmaR, double* diagG, void* stream) {
+  return solve(h, E, nE, sigmaL, sigmaR, 0.0, 0.0, nullptr, 0, diagG, nullptr, nullptr, stream, false);
+}
+
+int find_solve_lesser(find_handle* h, const double* E, int nE, const double* sigmaL,
+                      const double* sigmaR, double fL, double fR, const double* sigma_lesser_diag,
+                      int diag_per_energy, double* diagG, double* diagGl, double* bond_current,
+                      void* stream) {
+  return solve(h, E, nE, sigmaL, sigmaR, fL, fR, sigma_lesser_diag, diag_per_energy, diagG, diagGl,
+               bond_current, stream, true);
+}
+
+int find_destroy(find_handle* h) {
+  if (!h) return FIND_OK;
+  {
+    DeviceGuard guard(h->desc.device);
+    release(h);
+  }
+  delete h;
+  return FIND_OK;
+}
+
+const char* find_last_error(const find_handle* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+"""The C-ABI library loads without a GPU, exports every symbol of
+include/find.h, validates its arguments, and its host plan (tree, boundary
+and private-inner sets, bond table, flop model) agrees with the oracle's
+independent computation of the same set rules (Sec. 2.1-2.2)."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import find as ofind
+from oracle import problem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1104_0623_gb300 import build
+    build.build()
+    import paper_1104_0623_gb300 as F
+    return F
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "find.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(find_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(F):
+    lib = ctypes.CDLL(F._abi.LIB_PATH)
+    syms = header_symbols()
+    assert "find_solve_lesser" in syms and "find_create" in syms
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) <= set(F._abi.EXPORTED)
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(nx=0, ny=4), "nx"), (dict(nx=4, ny=1), "ny"), (dict(nx=4, ny=4, stencil=7), "stencil"),
+])
+def test_create_rejects_bad_arguments(F, kw, msg):
+    args = dict(nx=4, ny=4, stencil=5)
+    args.update(kw)
+    with pytest.raises(F.FindError) as ei:
+        F.Find(**args)
+    assert ei.value.code == 1 and msg in str(ei.value)
+
+
+def test_solve_rejects_null_outputs(F):
+    f = F.Find(4, 4)
+    with pytest.raises(F.FindError) as ei:
+        F.find_solve_diag(f.handle, None, 1, None, None, None, None)
+    assert ei.value.code == 1
+    f.close()
+
+
+def oracle_plan(nx, ny, stencil, leaf):
+    tree = ofind.build_tree(nx, ny, leaf)
+    B, Bb = ofind.boundary_sets(tree, problem.find_pattern(nx, ny, stencil), nx)
+    ss, bs, kn = [], [], []
+    fl_d = fl_l = 0.0
+    for k, c in enumerate(tree):
+        if k != 0:
+            if c.children:
+                merged = np.union1d(B[c.children[0]], B[c.children[1]])
+            else:
+                merged = c.nodes
+            s, b = len(np.setdiff1d(merged, B[k])), len(B[k])
+            ss.append(s); bs.append(b)
+            fl_d += 8 * (s ** 3 / 3 + s * s * b + s * b * b)
+            fl_l += 8 * (s ** 3 / 3 + s * s * b + s * b * b + s * s * b + 3 * s * b * b)
+            D = tree[c.parent]
+            d1 = D.children[1] if D.children[0] == k else D.children[0]
+            mergedb = B[d1] if c.parent == 0 else np.union1d(Bb[c.parent], B[d1])
+            s, b = len(np.setdiff1d(mergedb, Bb[k])), len(Bb[k])
+            ss.append(s); bs.append(b)
+            fl_d += 8 * (s ** 3 / 3 + s * s * b + s * b * b)
+            fl_l += 8 * (s ** 3 / 3 + s * s * b + s * b * b + s * s * b + 3 * s * b * b)
+        if not c.children:
+            nb, cc = (0 if k == 0 else len(Bb[k])), len(c.nodes)
+            kn.append(nb + cc)
+            fl_d += 8 * (nb ** 3 / 3 + nb * nb * cc + nb * cc * cc) + 8 * cc ** 3
+            fl_l += 8 * (nb ** 3 / 3 + 2 * nb * nb * cc + 4 * nb * cc * cc) + 24 * cc ** 3
+    return dict(n_clusters=len(tree), n_leaves=len(kn), max_s=max(ss, default=0),
+                max_b=max(bs, default=0), max_kn=max(kn), flops_diag=fl_d, flops_lesser=fl_l)
+
+
+@pytest.mark.parametrize("nx,ny,stencil,leaf", [(16, 16, 5, 4), (13, 17, 9, 4), (40, 40, 5, 5),
+                                               (7, 30, 9, 3), (3, 4, 9, 8), (64, 128, 5, 8)])
+def test_plan_matches_oracle_sets(F, nx, ny, stencil, leaf):
+    f = F.Find(nx, ny, stencil, 1.0, 0.2 if stencil == 9 else 0.0, leaf=leaf)
+    s = f.stats
+    ref = oracle_plan(nx, ny, stencil, leaf)
+    for key in ("n_clusters", "n_leaves", "max_s", "max_b", "max_kn"):
+        assert getattr(s, key) == ref[key], key
+    assert abs(s.flops_diag - ref["flops_diag"]) <= 1e-9 * ref["flops_diag"]
+    assert abs(s.flops_lesser - ref["flops_lesser"]) <= 1e-9 * ref["flops_lesser"]
+    from oracle.dense import bond_list
+    assert s.n_bonds == len(bond_list(nx, ny, stencil)[0])
+    f.close()
+
+
+def test_workspace_grows_linearly_with_batch(F):
+    f = F.Find(64, 128)
+    one, two, four = (f.workspace_bytes(b) for b in (1, 2, 4))
+    assert two > one and abs((four - two) - 2 * (two - one)) <= 4096 * 64
+    f.close()
+
+
+@pytest.mark.parametrize("nx,ny,stencil,leaf", [(16, 16, 5, 4), (13, 17, 9, 3), (37, 21, 9, 4),
+                                               (1, 23, 5, 2), (9, 2, 9, 2), (3, 4, 9, 8),
+                                               (128, 512, 5, 8), (256, 1024, 9, 8)])
+def test_descriptor_tables_stay_in_bounds(F, nx, ny, stencil, leaf):
+    # every operand of every kernel launch lies inside the workspace, for
+    # several batch sizes, in both the diag and the lesser configuration
+    f = F.Find(nx, ny, stencil, 1.0, 0.2, leaf=leaf)
+    for batch in (1, 3, 8):
+        for lesser in (False, True):
+            assert f.workspace_bytes(batch, lesser) > 0
+    f.close()
