@@ -20,11 +20,12 @@
  *   - complex numbers are interleaved (re, im) pairs of double; "k complex"
  *     below means 2k doubles.
  *   - array pointers may be HOST or DEVICE memory; the library asks the CUDA
- *     runtime which one it is.  Host inputs are staged to the device on the
- *     given stream; host outputs are copied back and the call returns after
- *     the stream has reached them.  With device pointers the call is
- *     asynchronous on `stream` and its status reflects launch errors only;
- *     numerical status (singular pivot) is read back at the end of the call.
+ *     runtime which one it is.  Host inputs are copied to the device on the
+ *     given stream and host outputs are copied back.  A solve enqueues all
+ *     of its work on `stream` and returns once the stream has completed it
+ *     (it reads back the device status word of singular pivots), so every
+ *     output is ready when the call returns.
+ *   - one handle serves one host thread at a time; handles are independent.
  *   - ownership: the caller owns every array it passes; the handle owns the
  *     plan, the index tables and the resident U/R workspace.
  *   - errors: every call returns a FIND_* status; no partial outputs are
@@ -135,6 +136,28 @@ int find_solve_lesser(find_handle* h, const double* E, int nE,
                       const double* sigma_lesser_diag, int diag_per_energy,
                       double* diagG, double* diagGl, double* bond_current,
                       void* stream);
+
+/* Per-kernel timing of the handle's solves (CUDA events recorded on the
+ * solve's stream around every launch while profiling is on).  Kernel
+ * classes: "lead", "assemble", "invert", "lu", "trsm", "zgemm32",
+ * "zgemm64", "extract".  flops are the algorithmic real flops of the
+ * launches (GEMM: 8 m n k per op and energy; LU: 8 s^3 / 3; triangular
+ * solves: 8 s^2 b; leaf inversion: 8 n^3), bytes the algorithmic DRAM bytes
+ * of the gather/extract kernels (blocks written plus source blocks read). */
+typedef struct {
+  char name[16];
+  int launches;
+  double ms;
+  double flops;
+  double bytes;
+} find_kernel_stat;
+
+/* enable = 1 clears the counters and starts recording; 0 stops. */
+int find_profile(find_handle* h, int enable);
+
+/* Waits for the recorded events and writes up to max entries; *count gets
+ * the number of kernel classes. */
+int find_profile_read(find_handle* h, find_kernel_stat* out, int max, int* count);
 
 /* Free the plan and the device workspace.  NULL is accepted. */
 int find_destroy(find_handle* h);

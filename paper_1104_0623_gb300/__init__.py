@@ -19,10 +19,12 @@ import numpy as np
 
 from . import _abi
 from ._abi import (FIND_FP64, FindError, find_create, find_destroy, find_last_error,  # noqa: F401
-                   find_plan_info, find_solve_diag, find_solve_lesser, find_workspace_bytes)
+                   find_plan_info, find_profile, find_profile_read, find_solve_diag,
+                   find_solve_lesser, find_workspace_bytes)
 
 __all__ = ["Find", "FindError", "find_create", "find_destroy", "find_last_error", "find_plan_info",
-           "find_solve_diag", "find_solve_lesser", "find_workspace_bytes"]
+           "find_profile", "find_profile_read", "find_solve_diag", "find_solve_lesser",
+           "find_workspace_bytes"]
 
 
 def _ptr(x, dtype_name):
@@ -86,10 +88,13 @@ class Find:
         return torch.cuda.current_stream(self.device).cuda_stream
 
     def _out(self, like, shape, dtype):
+        """Outputs live where the energies live: numpy, pinned host torch, or cuda."""
         if isinstance(like, np.ndarray):
             return np.empty(shape, dtype=dtype)
         import torch
         tdt = {np.complex128: torch.complex128, np.float64: torch.float64}[dtype]
+        if like.device.type == "cpu":
+            return torch.empty(shape, dtype=tdt, pin_memory=True)
         return torch.empty(shape, dtype=tdt, device=f"cuda:{self.device}")
 
     def solve_diag(self, E, sigmaL=None, sigmaR=None, stream=None, out=None):
@@ -118,6 +123,12 @@ class Find:
                           per_e, _ptr(dG, "complex128"), _ptr(dGl, "complex128"),
                           _ptr(J, "float64"), self._stream(stream))
         return dG, dGl, J
+
+    def profile(self, enable=True):
+        find_profile(self.handle, enable)
+
+    def profile_read(self):
+        return find_profile_read(self.handle)
 
     def workspace_bytes(self, batch, lesser=True):
         return find_workspace_bytes(self.handle, batch, lesser)

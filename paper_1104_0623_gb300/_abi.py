@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "FIND_OK", 1: "FIND_EINVAL", 2: "FIND_ENOMEM", 3: "FIND_ESING
                 4: "FIND_ETIMEOUT", 5: "FIND_ECUDA"}
 
 EXPORTED = ["find_create", "find_plan_info", "find_workspace_bytes", "find_solve_diag",
-            "find_solve_lesser", "find_destroy", "find_last_error"]
+            "find_solve_lesser", "find_profile", "find_profile_read", "find_destroy",
+            "find_last_error"]
 
 
 class find_desc(ctypes.Structure):
@@ -42,6 +43,11 @@ class find_plan_stats(ctypes.Structure):
                 ("scratch_bytes", ctypes.c_double)]
 
 
+class find_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 16), ("launches", ctypes.c_int), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -59,6 +65,8 @@ def load():
     lib.find_workspace_bytes.argtypes = [vp, ip, ip, ctypes.POINTER(dp)]
     lib.find_solve_diag.argtypes = [vp, vp, ip, vp, vp, vp, vp]
     lib.find_solve_lesser.argtypes = [vp, vp, ip, vp, vp, dp, dp, vp, ip, vp, vp, vp, vp]
+    lib.find_profile.argtypes = [vp, ip]
+    lib.find_profile_read.argtypes = [vp, ctypes.POINTER(find_kernel_stat), ip, ctypes.POINTER(ip)]
     lib.find_destroy.argtypes = [vp]
     lib.find_last_error.argtypes = [vp]
     lib.find_last_error.restype = ctypes.c_char_p
@@ -108,6 +116,19 @@ def find_solve_lesser(handle, E, nE, sigmaL, sigmaR, fL, fR, sigma_lesser_diag, 
     _check(load().find_solve_lesser(handle, E, nE, sigmaL, sigmaR, float(fL), float(fR),
                                     sigma_lesser_diag, int(diag_per_energy), diagG, diagGl,
                                     bond_current, stream), handle)
+
+
+def find_profile(handle: int, enable: bool) -> None:
+    _check(load().find_profile(handle, int(enable)), handle)
+
+
+def find_profile_read(handle: int):
+    """Per-kernel-class dicts: name, launches, ms, flops, bytes."""
+    arr = (find_kernel_stat * 16)()
+    cnt = ctypes.c_int()
+    _check(load().find_profile_read(handle, arr, 16, ctypes.byref(cnt)), handle)
+    return [dict(name=arr[k].name.decode(), launches=arr[k].launches, ms=arr[k].ms,
+                 flops=arr[k].flops, bytes=arr[k].bytes) for k in range(cnt.value)]
 
 
 def find_destroy(handle: int) -> None:

@@ -3,9 +3,11 @@
 //   k_lead_modes / k_lead_dense  lead self-energy closed form (per energy)
 //   k_assemble    gather M = [U_1 A_12; A_21 U_2] (and Sigma_M) ordered [S, B]
 //                 (Procedures updateBoundaryNodes / updateAdjacentNodes)
-//   k_invert      pivoted Gauss-Jordan inverse of M(S,S) in place
-//   k_zgemm       grouped complex GEMM: L = M(B,S) M(S,S)^{-1} (Eq. 13),
-//                 U = M(B,B) - L M(S,B) (Eq. 2),
+//   k_lu          pivoted LU of M(S,S) in place (one CTA per op and energy)
+//   k_trsm        L = M(B,S) M(S,S)^{-1} (Eq. 13) by two triangular sweeps,
+//                 row blocks spread over CTAs
+//   k_invert      pivoted Gauss-Jordan inverse of the bordered leaf system
+//   k_zgemm       grouped complex GEMM: U = M(B,B) - L M(S,B) (Eq. 2),
 //                 R = Sigma(B,B) - L Sigma(S,B) + (L Sigma(S,S) - Sigma(B,S)) L^H
 //                 (Eq. 7 regrouped), and the leaf products G_K Sigma_K G_K^H
 //   k_extract     diag G, diag G<, bond currents from the bordered leaves
@@ -269,6 +271,150 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(const InvOp* __restrict_
   }
 }
 
+// ---------------------------------------------------------------- LU factorisation
+// Right-looking LU with partial pivoting (largest |re| + |im|, first index on
+// ties) of the leading s x s block, in place: P M = L U with unit-lower L
+// below the diagonal.  Whole rows are interchanged, LAPACK style; piv[k] is
+// the row exchanged with row k at step k.  One CTA per (op, energy).  An
+// exactly zero pivot records the energy in *status and continues.
+__global__ void __launch_bounds__(kInvThreads) k_lu(const InvOp* __restrict__ ops,
+                                                    int* __restrict__ status, int e_base) {
+  const InvOp op = ops[blockIdx.x];
+  const int e = blockIdx.y;
+  const int s = op.s, ld = op.ld;
+  if (s == 0) return;
+  cplx* a = op.M + (int64_t)e * op.estride;
+  int* piv = op.piv + (int64_t)e * op.piv_estride;
+  extern __shared__ double2 lu_smem[];
+  cplx* rowk = lu_smem;
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int sh_p;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+
+  for (int k = 0; k < s; ++k) {
+    double best = -1.0;
+    int bi = INT_MAX;
+    for (int i = k + tid; i < s; i += blockDim.x) {
+      cplx v = a[(int64_t)i * ld + k];
+      double mg = fabs(v.x) + fabs(v.y);
+      if (mg > best) { best = mg; bi = i; }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      double ob = __shfl_down_sync(0xffffffffu, best, off);
+      int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < nwarp ? red_v[lane] : -1.0;
+      bi = lane < nwarp ? red_i[lane] : INT_MAX;
+      for (int off = 16; off > 0; off >>= 1) {
+        double ob = __shfl_down_sync(0xffffffffu, best, off);
+        int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        if (bi == INT_MAX) bi = k;
+        sh_p = bi;
+        piv[k] = bi;
+      }
+    }
+    __syncthreads();
+    const int p = sh_p;
+    if (p != k)
+      for (int j = tid; j < s; j += blockDim.x) {
+        cplx t0 = a[(int64_t)k * ld + j];
+        a[(int64_t)k * ld + j] = a[(int64_t)p * ld + j];
+        a[(int64_t)p * ld + j] = t0;
+      }
+    __syncthreads();
+    cplx pv = a[(int64_t)k * ld + k];
+    cplx pinv;
+    if (pv.x == 0.0 && pv.y == 0.0) {
+      pinv = cmk(0, 0);
+      if (tid == 0) atomicMin(status, e_base + e);
+    } else {
+      pinv = crecip(pv);
+    }
+    for (int j = k + 1 + tid; j < s; j += blockDim.x) rowk[j] = a[(int64_t)k * ld + j];
+    for (int i = k + 1 + tid; i < s; i += blockDim.x)
+      a[(int64_t)i * ld + k] = cmul(a[(int64_t)i * ld + k], pinv);
+    __syncthreads();
+    for (int i = k + 1 + warp; i < s; i += nwarp) {
+      cplx* row = a + (int64_t)i * ld;
+      const cplx l = row[k];
+      for (int j = k + 1 + lane; j < s; j += 32) row[j] = cfms(l, rowk[j], row[j]);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- L = M(B,S) M(S,S)^{-1}
+// Row block of RB rows per CTA held in shared memory.  Forward sweep solves
+// Y U = M(B,S) column by column (scale by 1/U_jj, then eliminate column j
+// from the later columns); backward sweep solves Z L = Y with the unit-lower
+// factor; the row interchanges are then applied as column interchanges.
+__global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
+                                              const int* __restrict__ tile_op, int rb) {
+  const TrsmOp& op = ops[tile_op[blockIdx.x]];
+  const int e = blockIdx.y;
+  const int s = op.s, ld = op.ld;
+  const int r0 = (blockIdx.x - op.tile0) * rb;
+  const int rows = min(rb, op.b - r0);
+  if (s == 0 || rows <= 0) return;
+  const cplx* a = op.M + (int64_t)e * op.estride;
+  const int* piv = op.piv + (int64_t)e * op.piv_estride;
+  extern __shared__ double2 tr_smem[];
+  cplx* Y = tr_smem;                               // rows x s
+  int* perm = reinterpret_cast<int*>(Y + (int64_t)rb * s);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int idx = tid; idx < rows * s; idx += nt) {
+    int r = idx / s, j = idx % s;
+    Y[r * s + j] = a[(int64_t)(s + r0 + r) * ld + j];
+  }
+  __syncthreads();
+  // forward: Y U = B
+  for (int j = 0; j < s; ++j) {
+    if (tid < rows) {
+      const cplx ujj = a[(int64_t)j * ld + j];  // zero only if the LU flagged it
+      cplx d = (ujj.x == 0.0 && ujj.y == 0.0) ? cmk(0, 0) : crecip(ujj);
+      Y[tid * s + j] = cmul(Y[tid * s + j], d);
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < s; i += nt) {
+      const cplx u = a[(int64_t)j * ld + i];
+      for (int r = 0; r < rows; ++r) Y[r * s + i] = cfms(Y[r * s + j], u, Y[r * s + i]);
+    }
+    __syncthreads();
+  }
+  // backward: Z L = Y, L unit lower
+  for (int j = s - 1; j > 0; --j) {
+    for (int i = tid; i < j; i += nt) {
+      const cplx l = a[(int64_t)j * ld + i];
+      for (int r = 0; r < rows; ++r) Y[r * s + i] = cfms(Y[r * s + j], l, Y[r * s + i]);
+    }
+    __syncthreads();
+  }
+  // L = Z P: column j of the result is column perm[j] of Z
+  if (tid == 0) {
+    for (int j = 0; j < s; ++j) perm[j] = j;
+    for (int k = s - 1; k >= 0; --k) {
+      int p = piv[k];
+      int t0 = perm[k];
+      perm[k] = perm[p];
+      perm[p] = t0;
+    }
+  }
+  __syncthreads();
+  cplx* L = op.L + (int64_t)e * op.l_estride;
+  for (int idx = tid; idx < rows * s; idx += nt) {
+    int r = idx / s, j = idx % s;
+    L[(int64_t)(r0 + r) * s + j] = Y[r * s + perm[j]];
+  }
+}
+
 // ---------------------------------------------------------------- grouped ZGEMM
 // Tile BM x BN per CTA, BK deep; each thread owns a 4 x 4 block of outputs at
 // rows ty + i*BM/4, cols tx + j*BN/4.  alpha is folded into the A tile.
@@ -415,6 +561,33 @@ void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_bas
   }
   dim3 grid(nops, nE);
   k_invert<<<grid, kInvThreads, smem, st>>>(ops, status, e_base);
+}
+
+void launch_lu(const InvOp* ops, int nops, int* status, int e_base, int nE, cudaStream_t st) {
+  if (nops == 0) return;
+  dim3 grid(nops, nE);
+  k_lu<<<grid, kInvThreads, kMaxInvert * sizeof(cplx), st>>>(ops, status, e_base);
+}
+
+constexpr int kTrsmSmem = 196608;
+
+int trsm_rows_per_block(int max_s) {
+  if (max_s <= 0) return 16;
+  int rb = (int)((kTrsmSmem - (int64_t)max_s * 4) / ((int64_t)max_s * sizeof(cplx)));
+  return rb < 1 ? 1 : (rb > 16 ? 16 : rb);
+}
+
+void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int max_s, int nE,
+                 cudaStream_t st) {
+  if (ntiles == 0 || max_s == 0) return;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
+    attr_set = true;
+  }
+  size_t smem = (size_t)rb * max_s * sizeof(cplx) + (size_t)max_s * sizeof(int);
+  dim3 grid(ntiles, nE);
+  k_trsm<<<grid, 256, smem, st>>>(ops, tile_op, rb);
 }
 
 void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,

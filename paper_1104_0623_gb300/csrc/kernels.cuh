@@ -35,11 +35,28 @@ struct AsmOp {
   int64_t estride;                         // per-energy stride of the op scratch
 };
 
-// In-place Gauss-Jordan inversion of the leading s x s block of M (ld).
+// In-place Gauss-Jordan inversion of the leading s x s block of M (ld); with
+// piv != nullptr, an in-place LU factorisation P M = L U of that block
+// instead (row interchanges in piv, LAPACK order).
 struct InvOp {
   cplx* M;
   int64_t estride;
   int ld, s;
+  int* piv;
+  int64_t piv_estride;
+};
+
+// L = M(B,S) M(S,S)^{-1} from the LU factors of M(S,S): rows r0..r0+rb of
+// M(B,S) per CTA; Y U = M(B,S), Z L = Y, L = Z P.
+struct TrsmOp {
+  const cplx* M;        // energy 0; M(S,S) holds the factors, M(B,S) the rows
+  int64_t estride;
+  int ld, s, b;
+  const int* piv;
+  int64_t piv_estride;
+  cplx* L;              // b x s, leading dimension s
+  int64_t l_estride;
+  int tile0;            // first row-block of this op in the launch
 };
 
 // D = beta * C + alpha * A op(B) + alpha2 * A2 op(B2); op(B) = B (opb 0) or
@@ -76,6 +93,10 @@ void launch_assemble(const AsmOp* ops, const int* row_op, int nrows, const Pos* 
                      const DevProblem& P, int lesser, int nE, cudaStream_t st);
 void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
                    cudaStream_t st);
+void launch_lu(const InvOp* ops, int nops, int* status, int e_base, int nE, cudaStream_t st);
+void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int max_s, int nE,
+                 cudaStream_t st);
+int trsm_rows_per_block(int max_s);
 void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,
                  cudaStream_t st);
 void launch_extract(const ExtractOp* ops, int nops, const LeafBond* bonds, const DevProblem& P,

@@ -63,12 +63,15 @@ struct Arena {
 struct Stage {
   size_t ops = 0, small = 0, big = 0;  // arena offsets
   int nsmall = 0, nbig = 0;
+  double fl_small = 0, fl_big = 0;     // algorithmic flops per energy of each tile class
 };
 
 struct Level {
   bool leaf = false;
   int nops = 0, nrows = 0, max_s = 0;
-  size_t asmops = 0, row_op = 0, inv = 0, ext = 0;  // arena offsets
+  int rb = 16, ntrsm = 0, nlu = 0;            // triangular-solve row block and counts
+  double fl_inv = 0, fl_lu = 0, fl_trsm = 0, by_asm = 0, by_ext = 0;  // per energy
+  size_t asmops = 0, row_op = 0, inv = 0, ext = 0, trsm = 0, trsm_map = 0;  // arena offsets
   Stage st[3];
   int nstages = 0;
 };
@@ -91,6 +94,12 @@ struct find_handle {
   Layout lay{};
   std::vector<Level> levels;  // upward, then downward, then the leaf level
   int n_up = 0, n_dn = 0;
+  // profiling
+  struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; };
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<Pending> pending;
+  find_kernel_stat stats[8];
 };
 
 namespace {
@@ -107,9 +116,10 @@ int cuda_fail(find_handle* h, cudaError_t e, const char* what) {
   return fail(h, e == cudaErrorMemoryAllocation ? FIND_ENOMEM : FIND_ECUDA, m);
 }
 
+// Per-energy scratch of one elimination: M [, Sigma_M], L [, T], pivots.
 int64_t op_slot_elems(const findgb::ElimOp& op, bool lesser) {
-  int64_t n = op.n, bs = (int64_t)op.b * op.s;
-  return lesser ? 2 * n * n + 2 * bs : n * n + bs;
+  int64_t n = op.n, bs = (int64_t)op.b * op.s, piv = (op.s + 3) / 4;
+  return (lesser ? 2 * n * n + 2 * bs : n * n + bs) + piv;
 }
 
 int64_t leaf_slot_elems(const findgb::LeafOp& op, bool lesser) {
@@ -119,9 +129,10 @@ int64_t leaf_slot_elems(const findgb::LeafOp& op, bool lesser) {
 
 // Adds one GEMM op to a stage, assigning its tiles to the small or big class.
 void add_gemm(findgb::GemmOp g, std::vector<findgb::GemmOp>& ops, std::vector<int>& small,
-              std::vector<int>& big) {
+              std::vector<int>& big, Stage* st = nullptr) {
   if (g.m == 0 || g.n == 0) return;
   bool is_big = std::max(g.m, g.n) > 32;
+  if (st) (is_big ? st->fl_big : st->fl_small) += 8.0 * g.m * g.n * (double)(g.k + (g.A2 ? g.k2 : 0));
   int bm = is_big ? 64 : 32;
   int tm = (g.m + bm - 1) / bm, tn = (g.n + bm - 1) / bm;
   std::vector<int>& map = is_big ? big : small;
@@ -189,8 +200,12 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     std::vector<findgb::AsmOp> asmops;
     std::vector<int> row_op;
     std::vector<findgb::InvOp> inv;
-    std::vector<findgb::GemmOp> g[3];
-    std::vector<int> sm[3], bg[3];
+    std::vector<findgb::TrsmOp> trs;
+    std::vector<int> trs_map;
+    std::vector<findgb::GemmOp> g[2];
+    std::vector<int> sm[2], bg[2];
+    for (const auto& op : ops) lv.max_s = std::max(lv.max_s, op.s);
+    lv.rb = findgb::trsm_rows_per_block(lv.max_s);
     int64_t off = 0;
     for (const auto& op : ops) {
       const int64_t slot = op_slot_elems(op, lesser);
@@ -198,6 +213,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       cplx* Sg = M + (int64_t)op.n * op.n;
       cplx* Lm = M + (lesser ? 2 : 1) * (int64_t)op.n * op.n;
       cplx* T = Lm + (int64_t)op.b * op.s;
+      int* piv = reinterpret_cast<int*>(Lm + (lesser ? 2 : 1) * (int64_t)op.b * op.s);
       off += slot;
       const int n = op.n, s = op.s, b = op.b;
       findgb::AsmOp a;
@@ -217,6 +233,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         if (a.u2) bc->block(a.u2, a.d2, a.d2, a.d2, (int64_t)a.d2 * a.d2, batch, "source U2");
         if (a.r1) bc->block(a.r1, a.d1, a.d1, a.d1, (int64_t)a.d1 * a.d1, batch, "source R1");
         if (a.r2) bc->block(a.r2, a.d2, a.d2, a.d2, (int64_t)a.d2 * a.d2, batch, "source R2");
+        if (s > 0) bc->block(reinterpret_cast<const cplx*>(piv), 1, (s + 3) / 4, (s + 3) / 4, slot, batch, "pivots");
         for (int q = 0; q < n && bc->err.empty(); ++q) {
           const findgb::Pos& pq = p.pos[op.pos + q];
           int d = pq.src == 1 ? a.d1 : pq.src == 2 ? a.d2 : 1;
@@ -224,33 +241,41 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
             bc->err = "assemble: gather index out of range";
         }
       }
-      inv.push_back(findgb::InvOp{M, slot, n, s});
-      lv.max_s = std::max(lv.max_s, s);
-      // stage 0: L = M(B,S) X, X = M(S,S)^{-1} in place   (Eq. 13)
+      if (s > 0) {
+        inv.push_back(findgb::InvOp{M, slot, n, s, piv, slot * 4});
+        lv.fl_lu += 8.0 * (double)s * s * s / 3.0;
+        if (b > 0) {
+          findgb::TrsmOp t;
+          t.M = M; t.estride = slot; t.ld = n; t.s = s; t.b = b;
+          t.piv = piv; t.piv_estride = slot * 4;
+          t.L = Lm; t.l_estride = slot;
+          t.tile0 = (int)trs_map.size();
+          for (int r = 0; r < (b + lv.rb - 1) / lv.rb; ++r) trs_map.push_back((int)trs.size());
+          trs.push_back(t);
+          lv.fl_trsm += 8.0 * (double)s * s * b;
+          if (bc) bc->block(Lm, b, s, s, slot, batch, "trsm L");
+        }
+      }
+      lv.by_asm += 16.0 * ((lesser ? 2.0 : 1.0) * n * n +
+                           (lesser ? 2.0 : 1.0) * ((double)a.d1 * a.d1 + (double)a.d2 * a.d2));
+      // stage 0: U = M(B,B) - L M(S,B)                        (Eq. 2)
       findgb::GemmOp q = gemm0();
-      q.m = b; q.n = s; q.k = s;
-      q.A = M + (int64_t)s * n; q.lda = n; q.sa = slot;
-      q.B = M; q.ldb = n; q.sb = slot;
-      q.D = Lm; q.ldd = s; q.sd = slot;
-      gemm_ok(q); add_gemm(q, g[0], sm[0], bg[0]);
-      // stage 1: U = M(B,B) - L M(S,B)                        (Eq. 2)
-      q = gemm0();
       q.m = b; q.n = b; q.k = s;
       q.A = Lm; q.lda = s; q.sa = slot; q.alpha = -1.0;
       q.B = M + s; q.ldb = n; q.sb = slot;
       q.C = M + (int64_t)s * n + s; q.ldc = n; q.sc = slot; q.beta = 1.0;
       q.D = umat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
-      gemm_ok(q); add_gemm(q, g[1], sm[1], bg[1]);
+      gemm_ok(q); add_gemm(q, g[0], sm[0], bg[0], &lv.st[0]);
       if (lesser) {
-        // stage 1: T = L Sigma(S,S) - Sigma(B,S)
+        // stage 0: T = L Sigma(S,S) - Sigma(B,S)
         q = gemm0();
         q.m = b; q.n = s; q.k = s;
         q.A = Lm; q.lda = s; q.sa = slot;
         q.B = Sg; q.ldb = n; q.sb = slot;
         q.C = Sg + (int64_t)s * n; q.ldc = n; q.sc = slot; q.beta = -1.0;
         q.D = T; q.ldd = s; q.sd = slot;
-        gemm_ok(q); add_gemm(q, g[1], sm[1], bg[1]);
-        // stage 2: R = Sigma(B,B) - L Sigma(S,B) + T L^H     (Eq. 7)
+        gemm_ok(q); add_gemm(q, g[0], sm[0], bg[0], &lv.st[0]);
+        // stage 1: R = Sigma(B,B) - L Sigma(S,B) + T L^H     (Eq. 7)
         q = gemm0();
         q.m = b; q.n = b; q.k = s; q.k2 = s;
         q.A = Lm; q.lda = s; q.sa = slot; q.alpha = -1.0;
@@ -259,14 +284,18 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         q.B2 = Lm; q.ldb2 = s; q.sb2 = slot; q.opb2 = 1;
         q.C = Sg + (int64_t)s * n + s; q.ldc = n; q.sc = slot; q.beta = 1.0;
         q.D = rmat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
-        gemm_ok(q); add_gemm(q, g[2], sm[2], bg[2]);
+        gemm_ok(q); add_gemm(q, g[1], sm[1], bg[1], &lv.st[1]);
       }
     }
     lv.nops = (int)ops.size();
     lv.asmops = ar.put(asmops);
     lv.row_op = ar.put(row_op);
     lv.inv = ar.put(inv);
-    lv.nstages = lesser ? 3 : 2;
+    lv.trsm = ar.put(trs);
+    lv.trsm_map = ar.put(trs_map);
+    lv.ntrsm = (int)trs_map.size();
+    lv.nlu = (int)inv.size();
+    lv.nstages = lesser ? 2 : 1;
     for (int k = 0; k < lv.nstages; ++k) {
       lv.st[k].ops = ar.put(g[k]);
       lv.st[k].small = ar.put(sm[k]);
@@ -329,8 +358,11 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
             bc->err = "leaf bond index out of range";
         }
       }
-      inv.push_back(findgb::InvOp{M, slot, n, n});
+      inv.push_back(findgb::InvOp{M, slot, n, n, nullptr, 0});
       lv.max_s = std::max(lv.max_s, n);
+      lv.fl_inv += 8.0 * (double)n * n * n;
+      lv.by_asm += 16.0 * ((lesser ? 2.0 : 1.0) * n * n + (lesser ? 2.0 : 1.0) * (double)a.d1 * a.d1);
+      lv.by_ext += 16.0 * (lesser ? 2.0 : 1.0) * op.c + (lesser ? 24.0 * op.nbond : 0.0);
       if (lesser) {
         // P = G_K(C, :) Sigma_K
         findgb::GemmOp q = gemm0();
@@ -338,14 +370,14 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         q.A = M + (int64_t)op.nb * n; q.lda = n; q.sa = slot;
         q.B = Sg; q.ldb = n; q.sb = slot;
         q.D = P; q.ldd = n; q.sd = slot;
-        gemm_ok(q); add_gemm(q, g[0], sm[0], bg[0]);
+        gemm_ok(q); add_gemm(q, g[0], sm[0], bg[0], &lv.st[0]);
         // Q = P G_K^H = G<_K(C, :)
         q = gemm0();
         q.m = op.c; q.n = n; q.k = n;
         q.A = P; q.lda = n; q.sa = slot;
         q.B = M; q.ldb = n; q.sb = slot; q.opb = 1;
         q.D = Q; q.ldd = n; q.sd = slot;
-        gemm_ok(q); add_gemm(q, g[1], sm[1], bg[1]);
+        gemm_ok(q); add_gemm(q, g[1], sm[1], bg[1], &lv.st[1]);
       }
       findgb::ExtractOp x;
       x.K = M;
@@ -498,26 +530,76 @@ const T* at(const find_handle* h, size_t off) {
   return reinterpret_cast<const T*>(h->ws + h->lay.meta + off);
 }
 
+const int kClasses = 8;
+const char* kClassNames[kClasses] = {"lead", "assemble", "invert", "lu", "trsm", "zgemm32", "zgemm64", "extract"};
+
+cudaEvent_t take_event(find_handle* h) {
+  if (!h->ev_free.empty()) {
+    cudaEvent_t e = h->ev_free.back();
+    h->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Runs `launch` on stream st; while profiling, brackets it with events.
+template <class F>
+void timed(find_handle* h, cudaStream_t st, int cls, double flops, double bytes, F&& launch) {
+  if (!h->prof) {
+    launch();
+    return;
+  }
+  cudaEvent_t a = take_event(h), b = take_event(h);
+  cudaEventRecord(a, st);
+  launch();
+  cudaEventRecord(b, st);
+  h->pending.push_back(find_handle::Pending{cls, a, b, flops, bytes});
+}
+
 void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, bool lesser,
                int e_base, int nb, cudaStream_t st, cplx* oG, cplx* oGl, double* oJ,
                int want_bonds) {
   const Layout& L = h->lay;
   auto pos = reinterpret_cast<const findgb::Pos*>(h->ws + L.pos);
   int* status = reinterpret_cast<int*>(h->ws + L.status);
-  findgb::launch_assemble(at<findgb::AsmOp>(h, lv.asmops), at<int>(h, lv.row_op), lv.nrows, pos, P,
-                          lesser ? 1 : 0, nb, st);
-  findgb::launch_invert(at<findgb::InvOp>(h, lv.inv), lv.nops, lv.max_s, status, e_base, nb, st);
+  timed(h, st, 1, 0.0, lv.by_asm * nb, [&] {
+    findgb::launch_assemble(at<findgb::AsmOp>(h, lv.asmops), at<int>(h, lv.row_op), lv.nrows, pos,
+                            P, lesser ? 1 : 0, nb, st);
+  });
+  if (lv.leaf) {
+    if (lv.max_s > 0)
+      timed(h, st, 2, lv.fl_inv * nb, 0.0, [&] {
+        findgb::launch_invert(at<findgb::InvOp>(h, lv.inv), lv.nops, lv.max_s, status, e_base, nb, st);
+      });
+  } else if (lv.nlu > 0) {
+    timed(h, st, 3, lv.fl_lu * nb, 0.0, [&] {
+      findgb::launch_lu(at<findgb::InvOp>(h, lv.inv), lv.nlu, status, e_base, nb, st);
+    });
+    if (lv.ntrsm > 0)
+      timed(h, st, 4, lv.fl_trsm * nb, 0.0, [&] {
+        findgb::launch_trsm(at<findgb::TrsmOp>(h, lv.trsm), at<int>(h, lv.trsm_map), lv.ntrsm, lv.rb,
+                            lv.max_s, nb, st);
+      });
+  }
   for (int k = 0; k < lv.nstages; ++k) {
     const Stage& s = lv.st[k];
     const findgb::GemmOp* ops = at<findgb::GemmOp>(h, s.ops);
-    findgb::launch_gemm(ops, at<int>(h, s.small), s.nsmall, 0, nb, st);
-    findgb::launch_gemm(ops, at<int>(h, s.big), s.nbig, 1, nb, st);
+    if (s.nsmall)
+      timed(h, st, 5, s.fl_small * nb, 0.0,
+            [&] { findgb::launch_gemm(ops, at<int>(h, s.small), s.nsmall, 0, nb, st); });
+    if (s.nbig)
+      timed(h, st, 6, s.fl_big * nb, 0.0,
+            [&] { findgb::launch_gemm(ops, at<int>(h, s.big), s.nbig, 1, nb, st); });
   }
   if (lv.leaf)
-    findgb::launch_extract(at<findgb::ExtractOp>(h, lv.ext), lv.nops,
-                           reinterpret_cast<const findgb::LeafBond*>(h->ws + L.bonds), P,
-                           lesser ? 1 : 0, want_bonds, oG, oGl, oJ,
-                           (int64_t)h->plan.nx * h->plan.ny, h->plan.n_bonds, nb, st);
+    timed(h, st, 7, 0.0, lv.by_ext * nb, [&] {
+      findgb::launch_extract(at<findgb::ExtractOp>(h, lv.ext), lv.nops,
+                             reinterpret_cast<const findgb::LeafBond*>(h->ws + L.bonds), P,
+                             lesser ? 1 : 0, want_bonds, oG, oGl, oJ,
+                             (int64_t)h->plan.nx * h->plan.ny, h->plan.n_bonds, nb, st);
+    });
 }
 
 int solve(find_handle* h, const double* E, int nE, const double* sigL, const double* sigR,
@@ -562,11 +644,13 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
     const cplx* useL = dsL;
     const cplx* useR = dsR;
     if (!sigL || !sigR) {
-      findgb::launch_lead_modes(dE, nb, reinterpret_cast<const double*>(ws + L.eps),
-                                reinterpret_cast<const double*>(ws + L.tau), (int)nx, dmodes, st);
       cplx* dst = !sigL ? dsL : dsR;
-      findgb::launch_lead_dense(dmodes, reinterpret_cast<const double*>(ws + L.phi), (int)nx, nb,
-                                dst, st);
+      timed(h, st, 0, 2.0 * nx * nx * nx * nb, 0.0, [&] {
+        findgb::launch_lead_modes(dE, nb, reinterpret_cast<const double*>(ws + L.eps),
+                                  reinterpret_cast<const double*>(ws + L.tau), (int)nx, dmodes, st);
+        findgb::launch_lead_dense(dmodes, reinterpret_cast<const double*>(ws + L.phi), (int)nx, nb,
+                                  dst, st);
+      });
       if (!sigL && !sigR) useR = dsL;
     }
     if (sigL) {
@@ -727,11 +811,55 @@ int find_solve_lesser(find_handle* h, const double* E, int nE, const double* sig
                bond_current, stream, true);
 }
 
+int find_profile(find_handle* h, int enable) {
+  if (!h) return FIND_EINVAL;
+  DeviceGuard guard(h->desc.device);
+  for (auto& p : h->pending) {
+    h->ev_free.push_back(p.a);
+    h->ev_free.push_back(p.b);
+  }
+  h->pending.clear();
+  if (enable) {
+    std::memset(h->stats, 0, sizeof(h->stats));
+    for (int k = 0; k < kClasses; ++k)
+      std::snprintf(h->stats[k].name, sizeof h->stats[k].name, "%s", kClassNames[k]);
+  }
+  h->prof = enable != 0;
+  return FIND_OK;
+}
+
+int find_profile_read(find_handle* h, find_kernel_stat* out, int max, int* count) {
+  if (!h || (!out && max > 0)) return FIND_EINVAL;
+  DeviceGuard guard(h->desc.device);
+  for (auto& p : h->pending) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(p.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.a, p.b);
+    if (e != cudaSuccess) return cuda_fail(h, e, "profile events");
+    find_kernel_stat& s = h->stats[p.cls];
+    s.launches += 1;
+    s.ms += ms;
+    s.flops += p.flops;
+    s.bytes += p.bytes;
+    h->ev_free.push_back(p.a);
+    h->ev_free.push_back(p.b);
+  }
+  h->pending.clear();
+  for (int k = 0; k < kClasses && k < max; ++k) out[k] = h->stats[k];
+  if (count) *count = kClasses;
+  return FIND_OK;
+}
+
 int find_destroy(find_handle* h) {
   if (!h) return FIND_OK;
   {
     DeviceGuard guard(h->desc.device);
     release(h);
+    for (auto& p : h->pending) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    for (auto e : h->ev_free) cudaEventDestroy(e);
   }
   delete h;
   return FIND_OK;
