@@ -137,7 +137,10 @@ class FindOracle:
                  tie: str = "y"):
         self.A = sp.csr_matrix(A, dtype=np.complex128)
         self.Sl = sp.csr_matrix(Sl, dtype=np.complex128)
+        self.A.sum_duplicates()
+        self.Sl.sum_duplicates()
         self.nx, self.ny = nx, ny
+        self._colpos = np.full(nx * ny, -1, np.int64)
         if pattern is None:
             pattern = self.A.copy()
             pattern.data = np.abs(pattern.data)
@@ -148,12 +151,27 @@ class FindOracle:
         self.B, self.Bbar = boundary_sets(self.tree, sp.csr_matrix(pattern), nx)
         self.U, self.R, self.Ubar, self.Rbar = {}, {}, {}, {}
 
-    # -- blocks of the original matrices
+    # -- blocks of the original matrices: Mat(rows, cols) as a dense array,
+    # read straight from the CSR rows through a column-position map
+    def _block(self, Mat, rows, cols):
+        pos = self._colpos
+        pos[cols] = np.arange(len(cols))
+        starts = Mat.indptr[rows]
+        counts = Mat.indptr[rows + 1] - starts
+        flat = np.repeat(starts - (np.cumsum(counts) - counts), counts) + np.arange(counts.sum())
+        r = np.repeat(np.arange(len(rows)), counts)
+        c = pos[Mat.indices[flat]]
+        keep = c >= 0
+        out = np.zeros((len(rows), len(cols)), np.complex128)
+        out[r[keep], c[keep]] = Mat.data[flat[keep]]
+        pos[cols] = -1
+        return out
+
     def _a(self, rows, cols):
-        return self.A[rows][:, cols].toarray()
+        return self._block(self.A, rows, cols)
 
     def _s(self, rows, cols):
-        return self.Sl[rows][:, cols].toarray()
+        return self._block(self.Sl, rows, cols)
 
     def _merge(self, n1, n2, U1, U2, R1, R2):
         M = np.block([[U1, self._a(n1, n2)], [self._a(n2, n1), U2]])
