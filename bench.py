@@ -1,0 +1,287 @@
+#!/usr/bin/env python
+"""Energy points per second of FIND (diag G, diag G< and bond currents) on the
+256x1024 9-point mesh (t' = 0.2 t, V ~ U[-1, 1] seed 1109, energies
+linspace(0.1, 7.9, 512) + 1e-6 i), FP64 path, one GB300 per rank.
+
+A step is one full FIND pass (lead self-energies, upward pass, downward pass,
+leaf extraction) over a batch of --batch energies.  Ranks take disjoint
+energies (weak scaling, no data-path collective).  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
+    python bench.py --impl reference ...   # the CPU oracle on the same workload
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "diag(G)+diag(G<) energy points/s at 256x1024"
+UNIT = "energy points/s"
+WORKLOAD = ("256x1024 mesh, 9-point stencil (t=1, t'=0.2), V~U[-1,1] seed 1109, "
+            "energies linspace(0.1,7.9,512)+1e-6i, outputs diag G, diag G<, bond currents")
+# FP64 peak of the kernels (DFMA on the CUDA cores): nominal 1.25 TFLOP/s at the
+# 2070 MHz maximum SM clock, scaled by the SM clock sampled during the run.
+FP64_NOMINAL_TFLOPS = 1.25
+SM_MAX_MHZ_NOMINAL = 2070.0
+# DRAM traffic per launch of the dominant kernel class, from the ncu capture
+# summarised in profiles/zgemm64_c5_256x1024.md (None: not captured for the
+# current kernel build).
+DOMINANT_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=8, help="energies per step and rank")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mesh", default="256x1024",
+                    help="NXxNY of the 9-point mesh (smaller meshes only for profiling)")
+    return ap.parse_args()
+
+
+def bench_mesh(spec):
+    nx, ny = (int(v) for v in spec.lower().split("x"))
+    if (nx, ny) == (256, 1024):
+        return W.c5()
+    return W.Mesh(nx, ny, 9, 1.0, 0.2, -1.0, 1.0, 1109)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampler around the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def step_energies(Es, step, rank, world, batch):
+    idx = ((step * world + rank) * batch + np.arange(batch)) % len(Es)
+    return np.ascontiguousarray(Es[idx])
+
+
+def cpu_baseline(mesh, Es):
+    """The oracle (O-find) as it stands on one energy point of the workload."""
+    from oracle import find as ofind, problem
+    P = problem.MeshProblem.from_mesh(mesh)
+    E = Es[len(Es) // 2]
+    t = time.perf_counter()
+    ofind.find_outputs(P, E, leaf=8, bonds=False)
+    dt = time.perf_counter() - t
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"1 of 512 energy points (E={E.real:.4f}+1e-6i), diag G + diag G<, "
+                      f"numpy/LAPACK FP64 on all {cores} host cores, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import find as ofind, problem
+    mesh, Es = W.c5(), W.c5_energies()
+    P = problem.MeshProblem.from_mesh(mesh)
+    for k in range(args.warmup):
+        ofind.find_outputs(P, Es[k], leaf=8, bonds=False)
+    t = time.perf_counter()
+    for k in range(args.steps):
+        ofind.find_outputs(P, Es[args.warmup + k], leaf=8, bonds=False)
+    dt = time.perf_counter() - t
+    value = args.steps / dt
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "energies_per_step": 1, "leaf": 8,
+                      "parallelism": "host cores (numpy/LAPACK threads)"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": "1 energy point per step, diag G + diag G<"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = local
+    torch.cuda.set_device(device)
+    import paper_1104_0623_gb300 as F
+
+    mesh, Es = bench_mesh(args.mesh), W.c5_energies()
+    B = args.batch
+    f = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=B)
+    n, nb = mesh.n, f.n_bonds
+    dev = f"cuda:{device}"
+    E_dev = [torch.tensor(step_energies(Es, k, rank, ws, B), dtype=torch.complex128, device=dev)
+             for k in range(args.warmup + args.steps)]
+    dG = torch.empty((B, n), dtype=torch.complex128, device=dev)
+    dGl = torch.empty((B, n), dtype=torch.complex128, device=dev)
+    J = torch.empty((B, nb), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(device)
+
+    def step(k):
+        f.solve_lesser(E_dev[k], 1.0, 0.0, out=(dG, dGl, J), stream=stream.cuda_stream)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize(device)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(device)
+
+    clocks = Clocks(device)
+    f.profile(True)
+    clocks.start()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    prof = f.profile_read()
+    f.profile(False)
+    t = e0.elapsed_time(e1) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t = float(tt.item())
+    value = ws * args.steps * B / t
+
+    # end-to-end through the C ABI with pinned host buffers (copies inside)
+    e2e = None
+    if not args.no_e2e:
+        E_host = [torch.from_numpy(step_energies(Es, k, rank, ws, B)).pin_memory()
+                  for k in range(args.steps)]
+        hG = torch.empty((B, n), dtype=torch.complex128, pin_memory=True)
+        hGl = torch.empty((B, n), dtype=torch.complex128, pin_memory=True)
+        hJ = torch.empty((B, nb), dtype=torch.float64, pin_memory=True)
+        barrier()
+        th = time.perf_counter()
+        for k in range(args.steps):
+            f.solve_lesser(E_host[k], 1.0, 0.0, out=(hG, hGl, hJ), stream=stream.cuda_stream)
+        barrier()
+        te = time.perf_counter() - th
+        if ws > 1:
+            tt = torch.tensor([te], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": ws * args.steps * B / te, "unit": UNIT, "h2d_bytes_per_step": B * 16,
+               "d2h_bytes_per_step": B * n * 16 * 2 + B * nb * 8}
+
+    # roofline of the dominant kernel class (FP64 CUDA-core arithmetic)
+    sm_mhz = clk.get("sm_mhz") or SM_MAX_MHZ_NOMINAL
+    peak = FP64_NOMINAL_TFLOPS * sm_mhz / SM_MAX_MHZ_NOMINAL
+    compute = [p for p in prof if p["flops"] > 0]
+    dom = max(compute, key=lambda p: p["ms"])
+    achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
+    traffic = DOMINANT_TRAFFIC.get(dom["name"])
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": dom["name"],
+                "launches": dom["launches"], "ms": dom["ms"],
+                "peak_source": f"nominal FP64 {FP64_NOMINAL_TFLOPS} TFLOP/s x sampled SM clock "
+                               f"{sm_mhz:.0f}/{SM_MAX_MHZ_NOMINAL:.0f} MHz"}
+    path_flops = f.stats.flops_lesser * args.steps * B
+    path = {"achieved": path_flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": path_flops / t / 1e12 / peak,
+            "flops_per_energy": f.stats.flops_lesser}
+    kernels = {p["name"]: {"launches": p["launches"], "ms": round(p["ms"], 3),
+                           "share": p["ms"] / sum(q["ms"] for q in prof)} for p in prof if p["launches"]}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD if args.mesh == "256x1024" else f"{args.mesh} profiling case",
+                      "energies_per_step": B, "leaf": 8, "path": "fp64",
+                      "l2": f"inputs larger than L2: {f.workspace_bytes(B) / 2**30:.1f} GiB "
+                            f"resident U/R and scratch per step",
+                      "parallelism": f"energy-sharded x{ws}, no data-path collective"},
+           "clocks": clk, "gpu_launches": sum(p["launches"] for p in prof),
+           "roofline": roofline, "path_roofline": path, "kernels": kernels}
+    if e2e:
+        out["e2e"] = e2e
+    f.close()
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.mesh == "256x1024":
+        out["cpu_baseline"] = cpu_baseline(mesh, Es)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
