@@ -137,6 +137,39 @@ int find_solve_lesser(find_handle* h, const double* E, int nE,
                       double* diagG, double* diagGl, double* bond_current,
                       void* stream);
 
+/*
+ * diag(G) exactly as find_solve_diag computes it, without allocating any
+ * device memory.  The paper has no counterpart; this entry point exists for
+ * deployment.
+ *
+ * Who needs it: a caller that may not or cannot call cudaMalloc -- a host
+ * program whose own memory pool has already reserved the device memory, a
+ * plug-in whose host application owns every device allocation, or a service
+ * loop that must not allocate once it runs.  Every device buffer the solve
+ * needs (resident U blocks, per-level scratch, gather and descriptor tables,
+ * the status word) lives in one fixed 64 MiB array compiled into the
+ * library; each GPU that loads the library holds that array until the
+ * process exits.  Inputs and outputs are still the caller's (host or device
+ * pointers, as for find_solve_diag).
+ *
+ * Limit: a mesh whose working set for one energy exceeds 64 MiB is rejected
+ * with FIND_EINVAL and a message giving the size it needs (a 40x40 mesh
+ * fits several energies per pass; 128x512 does not fit).  Energies are solved
+ * in passes of as many as fit.
+ *
+ * Set-up: the first call on a device (with that device current) looks up the
+ * array's device address once; make that first call before any stream
+ * capture.
+ *
+ * Sharing: all calls, from every handle, use the same array and leave their
+ * data in it; each call uploads its own tables and clears its status word
+ * before use.  Calls that overlap on the GPU (other streams or threads at the
+ * same time) race on the array and return wrong results: serialise them.
+ */
+int find_solve_diag_static(find_handle* h, const double* E, int nE,
+                           const double* sigmaL, const double* sigmaR,
+                           double* diagG, void* stream);
+
 /* Per-kernel timing of the handle's solves (CUDA events recorded on the
  * solve's stream around every launch while profiling is on).  Kernel
  * classes: "lead", "assemble", "invert", "lu", "trsm", "zgemm32",

@@ -22,8 +22,8 @@ STATUS_NAMES = {0: "FIND_OK", 1: "FIND_EINVAL", 2: "FIND_ENOMEM", 3: "FIND_ESING
                 4: "FIND_ETIMEOUT", 5: "FIND_ECUDA"}
 
 EXPORTED = ["find_create", "find_plan_info", "find_workspace_bytes", "find_solve_diag",
-            "find_solve_lesser", "find_profile", "find_profile_read", "find_destroy",
-            "find_last_error"]
+            "find_solve_diag_static", "find_solve_lesser", "find_profile", "find_profile_read",
+            "find_destroy", "find_last_error"]
 
 
 class find_desc(ctypes.Structure):
@@ -64,6 +64,7 @@ def load():
     lib.find_plan_info.argtypes = [vp, ctypes.POINTER(find_plan_stats)]
     lib.find_workspace_bytes.argtypes = [vp, ip, ip, ctypes.POINTER(dp)]
     lib.find_solve_diag.argtypes = [vp, vp, ip, vp, vp, vp, vp]
+    lib.find_solve_diag_static.argtypes = [vp, vp, ip, vp, vp, vp, vp]
     lib.find_solve_lesser.argtypes = [vp, vp, ip, vp, vp, dp, dp, vp, ip, vp, vp, vp, vp]
     lib.find_profile.argtypes = [vp, ip]
     lib.find_profile_read.argtypes = [vp, ctypes.POINTER(find_kernel_stat), ip, ctypes.POINTER(ip)]
@@ -109,6 +110,12 @@ def find_workspace_bytes(handle: int, batch: int, lesser: bool) -> float:
 
 def find_solve_diag(handle, E, nE, sigmaL, sigmaR, diagG, stream):
     _check(load().find_solve_diag(handle, E, nE, sigmaL, sigmaR, diagG, stream), handle)
+
+
+def find_solve_diag_static(handle, E, nE, sigmaL, sigmaR, diagG, stream):
+    """find_solve_diag with every device buffer in the library's fixed 64 MiB
+    array: for callers that cannot allocate device memory (see find.h)."""
+    _check(load().find_solve_diag_static(handle, E, nE, sigmaL, sigmaR, diagG, stream), handle)
 
 
 def find_solve_lesser(handle, E, nE, sigmaL, sigmaR, fL, fR, sigma_lesser_diag, diag_per_energy,

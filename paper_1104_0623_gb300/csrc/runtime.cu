@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -81,6 +82,18 @@ struct Layout {  // byte offsets inside the workspace
       status, meta, total;
 };
 
+// Tables of one handle laid out in the fixed device scratch (see
+// find_solve_diag_static): the scratch address they were built for, the
+// batch that fits, the layout, the levels and the host copy of the
+// descriptor arena.
+struct StaticView {
+  unsigned char* base = nullptr;
+  int batch = 0;
+  Layout lay{};
+  std::vector<Level> levels;
+  std::vector<unsigned char> meta;
+};
+
 }  // namespace
 
 struct find_handle {
@@ -100,6 +113,8 @@ struct find_handle {
   std::vector<cudaEvent_t> ev_free;
   std::vector<Pending> pending;
   find_kernel_stat stats[8];
+  // tables for the fixed device scratch
+  StaticView sview;
 };
 
 namespace {
@@ -715,6 +730,191 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
   return FIND_OK;
 }
 
+// ---------------------------------------------------------------- fixed device scratch
+// Device memory of find_solve_diag_static, for callers that cannot allocate
+// device memory.  It lives as long as the library stays loaded, on every
+// device that uses it.
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 128;
+unsigned char* g_static_ptr[kMaxDevices] = {};
+
+// Device address of the fixed scratch on `device`, which must be current.
+// Looked up once per device; host code must never hand the symbol itself to a
+// kernel (it is a host-side stand-in, not a device address).
+cudaError_t static_scratch_address(int device, unsigned char** out) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[device] = static_cast<unsigned char*>(p);
+  }
+  *out = g_static_ptr[device];
+  return cudaSuccess;
+}
+
+// The diag pass on the tables of `sv` (no profiling).
+void run_level_static(find_handle* h, const StaticView& sv, const Level& lv,
+                      const findgb::DevProblem& P, int e_base, int nb, cudaStream_t st, cplx* oG) {
+  const Layout& L = sv.lay;
+  auto meta = [&](size_t off) { return sv.base + L.meta + off; };
+  auto pos = reinterpret_cast<const findgb::Pos*>(sv.base + L.pos);
+  int* status = reinterpret_cast<int*>(sv.base + L.status);
+  findgb::launch_assemble(reinterpret_cast<const findgb::AsmOp*>(meta(lv.asmops)),
+                          reinterpret_cast<const int*>(meta(lv.row_op)), lv.nrows, pos, P, 0, nb, st);
+  if (lv.leaf) {
+    if (lv.max_s > 0)
+      findgb::launch_invert(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv)), lv.nops, lv.max_s,
+                            status, e_base, nb, st);
+  } else if (lv.nlu > 0) {
+    findgb::launch_lu(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv)), lv.nlu, status, e_base, nb, st);
+    if (lv.ntrsm > 0)
+      findgb::launch_trsm(reinterpret_cast<const findgb::TrsmOp*>(meta(lv.trsm)),
+                          reinterpret_cast<const int*>(meta(lv.trsm_map)), lv.ntrsm, lv.rb, lv.max_s,
+                          nb, st);
+  }
+  for (int k = 0; k < lv.nstages; ++k) {
+    const Stage& s = lv.st[k];
+    auto ops = reinterpret_cast<const findgb::GemmOp*>(meta(s.ops));
+    findgb::launch_gemm(ops, reinterpret_cast<const int*>(meta(s.small)), s.nsmall, 0, nb, st);
+    findgb::launch_gemm(ops, reinterpret_cast<const int*>(meta(s.big)), s.nbig, 1, nb, st);
+  }
+  if (lv.leaf)
+    findgb::launch_extract(reinterpret_cast<const findgb::ExtractOp*>(meta(lv.ext)), lv.nops,
+                           reinterpret_cast<const findgb::LeafBond*>(sv.base + L.bonds), P, 0, 0, oG,
+                           nullptr, nullptr, (int64_t)h->plan.nx * h->plan.ny, h->plan.n_bonds, nb, st);
+}
+
+int solve_static(find_handle* h, const double* E, int nE, const double* sigL, const double* sigR,
+                 double* G, void* stream) {
+  if (!h) return fail(nullptr, FIND_EINVAL, "null handle");
+  if (nE < 0) return fail(h, FIND_EINVAL, "nE < 0");
+  if (nE == 0) return FIND_OK;
+  if (!E || !G) return fail(h, FIND_EINVAL, "E and diagG must not be NULL");
+  DeviceGuard guard(h->desc.device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  unsigned char* base = nullptr;
+  cudaError_t e = static_scratch_address(h->desc.device, &base);
+  if (e != cudaSuccess) return cuda_fail(h, e, "fixed scratch address");
+  StaticView& sv = h->sview;
+  if (sv.base != base) {
+    // size the largest energy batch that fits, then lay the tables out on it
+    int batch = 0;
+    double need1 = workspace_bytes(h, 1, false);
+    for (int b = 1; b <= 64; ++b) {
+      if (workspace_bytes(h, b, false) > (double)kStaticScratchBytes) break;
+      batch = b;
+    }
+    if (batch == 0) {
+      char buf[192];
+      std::snprintf(buf, sizeof buf,
+                    "this mesh needs %.1f MiB of device scratch for one energy; the fixed scratch of "
+                    "find_solve_diag_static holds %.0f MiB",
+                    need1 / 1048576.0, (double)kStaticScratchBytes / 1048576.0);
+      return fail(h, FIND_EINVAL, buf);
+    }
+    Arena sizing;
+    std::vector<Level> lv;
+    int64_t se = 0;
+    Layout L0 = make_layout(h, batch, false, 0, 0);
+    build_tables(h, nullptr, L0, batch, false, sizing, lv, se);
+    Layout L = make_layout(h, batch, false, se, sizing.buf.size());
+    Arena real;
+    Bounds bc;
+    bc.lo = base;
+    bc.hi = base + L.meta;
+    build_tables(h, base, L, batch, false, real, lv, se, &bc);
+    if (!bc.err.empty() || L.total > kStaticScratchBytes)
+      return fail(h, FIND_EINVAL, "internal table check failed for the fixed scratch: " + bc.err);
+    sv.base = base;
+    sv.batch = batch;
+    sv.lay = L;
+    sv.levels = std::move(lv);
+    sv.meta = std::move(real.buf);
+  }
+  const findgb::Plan& p = h->plan;
+  const Layout& L = sv.lay;
+  const int64_t n = (int64_t)p.nx * p.ny, nx = p.nx;
+  // the array is shared by every handle: upload this handle's constants and
+  // tables on each call, and clear the status word
+  struct Up { size_t off; const void* src; size_t bytes; } ups[] = {
+      {L.V, h->V.data(), h->V.size() * 8},
+      {L.phi, h->phi.data(), h->phi.size() * 8},
+      {L.eps, h->eps.data(), h->eps.size() * 8},
+      {L.tau, h->tau.data(), h->tau.size() * 8},
+      {L.pos, p.pos.data(), p.pos.size() * sizeof(findgb::Pos)},
+      {L.bonds, p.bonds.data(), p.bonds.size() * sizeof(findgb::LeafBond)},
+      {L.meta, sv.meta.data(), sv.meta.size()}};
+  for (const Up& u : ups) {
+    if (u.bytes == 0) continue;
+    e = cudaMemcpyAsync(base + u.off, u.src, u.bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "fixed scratch upload");
+  }
+  int* status = reinterpret_cast<int*>(base + L.status);
+  e = cudaMemsetAsync(status, 0x7f, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
+  const int kNoError = 0x7f7f7f7f;
+  cplx* dE = reinterpret_cast<cplx*>(base + L.E);
+  cplx* dsL = reinterpret_cast<cplx*>(base + L.sigL);
+  cplx* dsR = reinterpret_cast<cplx*>(base + L.sigR);
+  cplx* dmodes = reinterpret_cast<cplx*>(base + L.modes);
+  const bool dG = device_accessible(G);
+  for (int e0 = 0; e0 < nE; e0 += sv.batch) {
+    const int nb = std::min(sv.batch, nE - e0);
+    e = cudaMemcpyAsync(dE, E + 2 * (int64_t)e0, nb * sizeof(cplx), cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "energy copy");
+    const cplx* useL = dsL;
+    const cplx* useR = dsR;
+    if (!sigL || !sigR) {
+      cplx* dst = !sigL ? dsL : dsR;
+      findgb::launch_lead_modes(dE, nb, reinterpret_cast<const double*>(base + L.eps),
+                                reinterpret_cast<const double*>(base + L.tau), (int)nx, dmodes, st);
+      findgb::launch_lead_dense(dmodes, reinterpret_cast<const double*>(base + L.phi), (int)nx, nb, dst, st);
+      if (!sigL && !sigR) useR = dsL;
+    }
+    if (sigL) {
+      e = cudaMemcpyAsync(dsL, sigL + 2 * (int64_t)e0 * nx * nx, nb * nx * nx * sizeof(cplx),
+                          cudaMemcpyDefault, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "sigmaL copy");
+    }
+    if (sigR) {
+      e = cudaMemcpyAsync(dsR, sigR + 2 * (int64_t)e0 * nx * nx, nb * nx * nx * sizeof(cplx),
+                          cudaMemcpyDefault, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "sigmaR copy");
+    }
+    findgb::DevProblem P;
+    P.nx = p.nx; P.ny = p.ny; P.stencil = p.stencil;
+    P.t = h->desc.t; P.tp = h->desc.tp; P.onsite0 = h->desc.onsite0;
+    P.V = reinterpret_cast<const double*>(base + L.V);
+    P.E = dE; P.sigL = useL; P.sigR = useR;
+    P.fL = 0.0; P.fR = 0.0;
+    P.dles = nullptr; P.dles_estride = 0;
+    cplx* oG = dG ? reinterpret_cast<cplx*>(G) + (int64_t)e0 * n : reinterpret_cast<cplx*>(base + L.oG);
+    for (const Level& lv : sv.levels) run_level_static(h, sv, lv, P, e0, nb, st, oG);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+    if (!dG) {
+      e = cudaMemcpyAsync(G + 2 * (int64_t)e0 * n, oG, nb * n * sizeof(cplx), cudaMemcpyDefault, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "diagG copy-out");
+    }
+  }
+  int hs = kNoError;
+  e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "solve");
+  if (hs != kNoError) {
+    char buf[128];
+    std::snprintf(buf, sizeof buf, "exactly zero pivot at energy index %d", hs);
+    return fail(h, FIND_ESINGULAR, buf);
+  }
+  h->err.clear();
+  return FIND_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -801,6 +1001,11 @@ int find_workspace_bytes(const find_handle* h, int batch, int lesser, double* by
 int find_solve_diag(find_handle* h, const double* E, int nE, const double* sigmaL,
                     const double* sigmaR, double* diagG, void* stream) {
   return solve(h, E, nE, sigmaL, sigmaR, 0.0, 0.0, nullptr, 0, diagG, nullptr, nullptr, stream, false);
+}
+
+int find_solve_diag_static(find_handle* h, const double* E, int nE, const double* sigmaL,
+                           const double* sigmaR, double* diagG, void* stream) {
+  return solve_static(h, E, nE, sigmaL, sigmaR, diagG, stream);
 }
 
 int find_solve_lesser(find_handle* h, const double* E, int nE, const double* sigmaL,
