@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--path", choices=["fp64", "mixed"], default="fp64",
+                    help="fp64: every step in FP64; mixed: Sigma update and leaf G< "
+                         "products in complex64, the rest FP64")
     ap.add_argument("--mesh", default="256x1024",
                     help="NXxNY of the 9-point mesh (smaller meshes only for profiling)")
     return ap.parse_args()
@@ -180,7 +183,7 @@ def main():
 
     mesh, Es = bench_mesh(args.mesh), W.c5_energies()
     B = args.batch
-    f = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=B)
+    f = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=B, precision=args.path)
     n, nb = mesh.n, f.n_bonds
     dev = f"cuda:{device}"
     E_dev = [torch.tensor(step_energies(Es, k, rank, ws, B), dtype=torch.complex128, device=dev)
@@ -266,7 +269,7 @@ def main():
            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD if args.mesh == "256x1024" else f"{args.mesh} profiling case",
-                      "energies_per_step": B, "leaf": 8, "path": "fp64",
+                      "energies_per_step": B, "leaf": 8, "path": args.path,
                       "l2": f"inputs larger than L2: {f.workspace_bytes(B) / 2**30:.1f} GiB "
                             f"resident U/R and scratch per step",
                       "parallelism": f"energy-sharded x{ws}, no data-path collective"},

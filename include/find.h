@@ -48,7 +48,17 @@ enum {
   FIND_ECUDA = 5       /* any other CUDA runtime error                      */
 };
 
-enum { FIND_FP64 = 0 };
+/* FIND_FP64: every step in FP64.
+ * FIND_MIXED: the Sigma update (Eq. 7: T = L Sigma(S,S) - Sigma(B,S) and
+ * R = Sigma(B,B) - L Sigma(S,B) + T L^H) and the leaf products
+ * G_K Sigma_K G_K^H run in complex64 arithmetic (operands and results stay
+ * complex128 in memory); the Schur update U (Eq. 2), the pivoted LU, the
+ * triangular solves for L (Eq. 13), the leaf inversion and every step of the
+ * top fp64_top_levels tree levels stay FP64.  Complex64 in the U update was
+ * measured to lose up to 2.5e-3 (cancellation in ill-conditioned inner
+ * blocks, amplified by later eliminations); in the Sigma update it costs
+ * about 1e-6. */
+enum { FIND_FP64 = 0, FIND_MIXED = 1 };
 
 typedef struct find_handle find_handle;
 
@@ -60,10 +70,13 @@ typedef struct {
                                find_create; NULL means V = 0                   */
   double onsite0;           /* clean onsite energy (4t, or 4t + 4tp for 9)     */
   int leaf;                 /* leaf clusters have both sides <= leaf; 0 = 8    */
-  int precision;            /* FIND_FP64                                       */
+  int precision;            /* FIND_FP64 or FIND_MIXED                         */
   int device;               /* CUDA device ordinal                             */
   int max_batch;            /* energies solved together; 0 = chosen from free
                                device memory                                   */
+  int fp64_top_levels;      /* FIND_MIXED: tree depths 1..fp64_top_levels (the
+                               root's children are depth 1) stay FP64; < 0
+                               means the default 2                             */
 } find_desc;
 
 /* Host-side facts of the plan (no GPU needed). */
@@ -173,7 +186,8 @@ int find_solve_diag_static(find_handle* h, const double* E, int nE,
 /* Per-kernel timing of the handle's solves (CUDA events recorded on the
  * solve's stream around every launch while profiling is on).  Kernel
  * classes: "lead", "assemble", "invert", "lu", "trsm", "zgemm32",
- * "zgemm64", "extract".  flops are the algorithmic real flops of the
+ * "zgemm64", "extract", "cgemm32", "cgemm64" (z: FP64, c: complex64
+ * arithmetic; 32/64: tile size).  flops are the algorithmic real flops of the
  * launches (GEMM: 8 m n k per op and energy; LU: 8 s^3 / 3; triangular
  * solves: 8 s^2 b; leaf inversion: 8 n^3), bytes the algorithmic DRAM bytes
  * of the gather/extract kernels (blocks written plus source blocks read). */

@@ -7,7 +7,8 @@
 //   k_trsm        L = M(B,S) M(S,S)^{-1} (Eq. 13) by two triangular sweeps,
 //                 row blocks spread over CTAs
 //   k_invert      pivoted Gauss-Jordan inverse of the bordered leaf system
-//   k_zgemm       grouped complex GEMM: U = M(B,B) - L M(S,B) (Eq. 2),
+//   k_zgemm       grouped complex GEMM (FP64, or complex64 arithmetic in the
+//                 mixed path): U = M(B,B) - L M(S,B) (Eq. 2),
 //                 R = Sigma(B,B) - L Sigma(S,B) + (L Sigma(S,S) - Sigma(B,S)) L^H
 //                 (Eq. 7 regrouped), and the leaf products G_K Sigma_K G_K^H
 //   k_extract     diag G, diag G<, bond currents from the bordered leaves
@@ -415,27 +416,58 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
   }
 }
 
-// ---------------------------------------------------------------- grouped ZGEMM
+// ---------------------------------------------------------------- grouped complex GEMM
+// Operands are complex128 in memory; CT is the arithmetic type: double2 (FP64
+// path) or float2 (complex64 arithmetic of the mixed path, operands rounded
+// when staged in shared memory, the epilogue adds beta * C in FP64).
+template <class CT>
+struct Cx;
+
+template <>
+struct Cx<double2> {
+  __device__ __forceinline__ static double2 zero() { return make_double2(0.0, 0.0); }
+  __device__ __forceinline__ static double2 load(cplx v, double a) { return make_double2(v.x * a, v.y * a); }
+  __device__ __forceinline__ static double2 fma(double2 a, double2 b, double2 c) { return cfma(a, b, c); }
+  __device__ __forceinline__ static cplx wide(double2 v) { return v; }
+};
+
+template <>
+struct Cx<float2> {
+  __device__ __forceinline__ static float2 zero() { return make_float2(0.f, 0.f); }
+  __device__ __forceinline__ static float2 load(cplx v, double a) {
+    return make_float2((float)(v.x * a), (float)(v.y * a));
+  }
+  __device__ __forceinline__ static float2 fma(float2 a, float2 b, float2 c) {
+    c.x = fmaf(a.x, b.x, c.x);
+    c.x = fmaf(-a.y, b.y, c.x);
+    c.y = fmaf(a.x, b.y, c.y);
+    c.y = fmaf(a.y, b.x, c.y);
+    return c;
+  }
+  __device__ __forceinline__ static cplx wide(float2 v) { return make_double2(v.x, v.y); }
+};
+
 // Tile BM x BN per CTA, BK deep; each thread owns a 4 x 4 block of outputs at
 // rows ty + i*BM/4, cols tx + j*BN/4.  alpha is folded into the A tile.
-template <int BM, int BN, int BK>
+template <int BM, int BN, int BK, class CT>
 __global__ void __launch_bounds__((BM / 4) * (BN / 4)) k_zgemm(const GemmOp* __restrict__ ops,
                                                                const int* __restrict__ tile_op) {
+  typedef Cx<CT> X;
   constexpr int NT = (BM / 4) * (BN / 4);
   constexpr int RS = BM / 4, CS = BN / 4;
-  __shared__ cplx As[BK][BM + 1];
-  __shared__ cplx Bs[BK][BN + 1];
+  __shared__ CT As[BK][BM + 1];
+  __shared__ CT Bs[BK][BN + 1];
   const int t = blockIdx.x, e = blockIdx.y;
   const GemmOp& op = ops[tile_op[t]];
   const int local = t - op.tile0;
   const int m0 = (local / op.tiles_n) * BM, n0 = (local % op.tiles_n) * BN;
   const int tx = threadIdx.x % CS, ty = threadIdx.x / CS;
   const int M = op.m, N = op.n;
-  cplx acc[4][4];
+  CT acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = cmk(0, 0);
+    for (int j = 0; j < 4; ++j) acc[i][j] = X::zero();
 
   for (int pass = 0; pass < 2; ++pass) {
     const cplx* A = pass ? op.A2 : op.A;
@@ -452,25 +484,25 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4)) k_zgemm(const GemmOp* __r
         int i = idx / BK, kk = idx % BK;
         int gi = m0 + i, gk = k0 + kk;
         cplx v = (gi < M && gk < K) ? A[(int64_t)gi * lda + gk] : cmk(0, 0);
-        As[kk][i] = cscale(v, alpha);
+        As[kk][i] = X::load(v, alpha);
       }
       if (opb == 0) {
         for (int idx = threadIdx.x; idx < BK * BN; idx += NT) {
           int kk = idx / BN, j = idx % BN;
           int gk = k0 + kk, gj = n0 + j;
-          Bs[kk][j] = (gk < K && gj < N) ? B[(int64_t)gk * ldb + gj] : cmk(0, 0);
+          Bs[kk][j] = X::load((gk < K && gj < N) ? B[(int64_t)gk * ldb + gj] : cmk(0, 0), 1.0);
         }
       } else {
         for (int idx = threadIdx.x; idx < BK * BN; idx += NT) {
           int j = idx / BK, kk = idx % BK;
           int gk = k0 + kk, gj = n0 + j;
-          Bs[kk][j] = (gk < K && gj < N) ? cconj(B[(int64_t)gj * ldb + gk]) : cmk(0, 0);
+          Bs[kk][j] = X::load((gk < K && gj < N) ? cconj(B[(int64_t)gj * ldb + gk]) : cmk(0, 0), 1.0);
         }
       }
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        cplx av[4], bv[4];
+        CT av[4], bv[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + i * RS];
 #pragma unroll
@@ -478,7 +510,7 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4)) k_zgemm(const GemmOp* __r
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = cfma(av[i], bv[j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) acc[i][j] = X::fma(av[i], bv[j], acc[i][j]);
       }
       __syncthreads();
     }
@@ -493,7 +525,7 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4)) k_zgemm(const GemmOp* __r
     for (int j = 0; j < 4; ++j) {
       int gj = n0 + tx + j * CS;
       if (gj >= N) continue;
-      cplx v = acc[i][j];
+      cplx v = X::wide(acc[i][j]);
       if (C) {
         cplx c = C[(int64_t)gi * op.ldc + gj];
         v.x = fma(op.beta, c.x, v.x);
@@ -591,13 +623,20 @@ void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int 
 }
 
 void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,
-                 cudaStream_t st) {
+                 cudaStream_t st, int fp32) {
   if (ntiles == 0) return;
   dim3 grid(ntiles, nE);
-  if (big)
-    k_zgemm<64, 64, 8><<<grid, 256, 0, st>>>(ops, tile_op);
-  else
-    k_zgemm<32, 32, 8><<<grid, 64, 0, st>>>(ops, tile_op);
+  if (fp32) {
+    if (big)
+      k_zgemm<64, 64, 16, float2><<<grid, 256, 0, st>>>(ops, tile_op);
+    else
+      k_zgemm<32, 32, 16, float2><<<grid, 64, 0, st>>>(ops, tile_op);
+  } else {
+    if (big)
+      k_zgemm<64, 64, 8, double2><<<grid, 256, 0, st>>>(ops, tile_op);
+    else
+      k_zgemm<32, 32, 8, double2><<<grid, 64, 0, st>>>(ops, tile_op);
+  }
 }
 
 void launch_extract(const ExtractOp* ops, int nops, const LeafBond* bonds, const DevProblem& P,

@@ -97,8 +97,9 @@ void launch_lu(const InvOp* ops, int nops, int* status, int e_base, int nE, cuda
 void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int max_s, int nE,
                  cudaStream_t st);
 int trsm_rows_per_block(int max_s);
+// fp32 = 1: complex64 arithmetic on complex128 operands (mixed path)
 void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,
-                 cudaStream_t st);
+                 cudaStream_t st, int fp32 = 0);
 void launch_extract(const ExtractOp* ops, int nops, const LeafBond* bonds, const DevProblem& P,
                     int lesser, int want_bonds, cplx* diagG, cplx* diagGl, double* J,
                     int64_t n_nodes, int64_t n_bonds, int nE, cudaStream_t st);

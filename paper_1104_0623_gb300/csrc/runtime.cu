@@ -61,10 +61,13 @@ struct Arena {
   }
 };
 
+// One GEMM stage of a level: its ops and the tile maps of the four launch
+// classes [FP64 small, FP64 big, complex64 small, complex64 big].
 struct Stage {
-  size_t ops = 0, small = 0, big = 0;  // arena offsets
-  int nsmall = 0, nbig = 0;
-  double fl_small = 0, fl_big = 0;     // algorithmic flops per energy of each tile class
+  size_t ops = 0;
+  size_t map[4] = {0, 0, 0, 0};  // arena offsets
+  int nmap[4] = {0, 0, 0, 0};
+  double fl[4] = {0, 0, 0, 0};   // algorithmic flops per energy of each class
 };
 
 struct Level {
@@ -112,7 +115,7 @@ struct find_handle {
   bool prof = false;
   std::vector<cudaEvent_t> ev_free;
   std::vector<Pending> pending;
-  find_kernel_stat stats[8];
+  find_kernel_stat stats[10];
   // tables for the fixed device scratch
   StaticView sview;
 };
@@ -143,14 +146,15 @@ int64_t leaf_slot_elems(const findgb::LeafOp& op, bool lesser) {
 }
 
 // Adds one GEMM op to a stage, assigning its tiles to the small or big class.
-void add_gemm(findgb::GemmOp g, std::vector<findgb::GemmOp>& ops, std::vector<int>& small,
-              std::vector<int>& big, Stage* st = nullptr) {
+void add_gemm(findgb::GemmOp g, std::vector<findgb::GemmOp>& ops, std::vector<int>* maps,
+              Stage* st, bool fp32) {
   if (g.m == 0 || g.n == 0) return;
   bool is_big = std::max(g.m, g.n) > 32;
-  if (st) (is_big ? st->fl_big : st->fl_small) += 8.0 * g.m * g.n * (double)(g.k + (g.A2 ? g.k2 : 0));
+  const int cls = (fp32 ? 2 : 0) + (is_big ? 1 : 0);
+  st->fl[cls] += 8.0 * g.m * g.n * (double)(g.k + (g.A2 ? g.k2 : 0));
   int bm = is_big ? 64 : 32;
   int tm = (g.m + bm - 1) / bm, tn = (g.n + bm - 1) / bm;
-  std::vector<int>& map = is_big ? big : small;
+  std::vector<int>& map = maps[cls];
   g.tile0 = (int)map.size();
   g.tiles_n = tn;
   int id = (int)ops.size();
@@ -196,6 +200,8 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
   auto rmat = [&](int id) { return (id < 0 || !R) ? (cplx*)nullptr : R + p.mat_off[id] * batch; };
   levels.clear();
   scratch_elems = 0;
+  const bool mixed = h->desc.precision == FIND_MIXED;
+  const int top_levels = h->desc.fp64_top_levels < 0 ? 2 : h->desc.fp64_top_levels;
   auto gemm_ok = [&](const findgb::GemmOp& q) {
     if (!bc || q.m == 0 || q.n == 0) return;
     bc->block(q.A, q.m, q.k, q.lda, q.sa, batch, "gemm A");
@@ -218,7 +224,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     std::vector<findgb::TrsmOp> trs;
     std::vector<int> trs_map;
     std::vector<findgb::GemmOp> g[2];
-    std::vector<int> sm[2], bg[2];
+    std::vector<int> maps[2][4];
     for (const auto& op : ops) lv.max_s = std::max(lv.max_s, op.s);
     lv.rb = findgb::trsm_rows_per_block(lv.max_s);
     int64_t off = 0;
@@ -280,7 +286,9 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       q.B = M + s; q.ldb = n; q.sb = slot;
       q.C = M + (int64_t)s * n + s; q.ldc = n; q.sc = slot; q.beta = 1.0;
       q.D = umat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
-      gemm_ok(q); add_gemm(q, g[0], sm[0], bg[0], &lv.st[0]);
+      gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], false);
+      // Sigma update in complex64 arithmetic below the top FP64 levels
+      const bool c64 = mixed && p.cl[op.cluster].depth > top_levels;
       if (lesser) {
         // stage 0: T = L Sigma(S,S) - Sigma(B,S)
         q = gemm0();
@@ -289,7 +297,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         q.B = Sg; q.ldb = n; q.sb = slot;
         q.C = Sg + (int64_t)s * n; q.ldc = n; q.sc = slot; q.beta = -1.0;
         q.D = T; q.ldd = s; q.sd = slot;
-        gemm_ok(q); add_gemm(q, g[0], sm[0], bg[0], &lv.st[0]);
+        gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], c64);
         // stage 1: R = Sigma(B,B) - L Sigma(S,B) + T L^H     (Eq. 7)
         q = gemm0();
         q.m = b; q.n = b; q.k = s; q.k2 = s;
@@ -299,7 +307,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         q.B2 = Lm; q.ldb2 = s; q.sb2 = slot; q.opb2 = 1;
         q.C = Sg + (int64_t)s * n + s; q.ldc = n; q.sc = slot; q.beta = 1.0;
         q.D = rmat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
-        gemm_ok(q); add_gemm(q, g[1], sm[1], bg[1], &lv.st[1]);
+        gemm_ok(q); add_gemm(q, g[1], maps[1], &lv.st[1], c64);
       }
     }
     lv.nops = (int)ops.size();
@@ -313,10 +321,10 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     lv.nstages = lesser ? 2 : 1;
     for (int k = 0; k < lv.nstages; ++k) {
       lv.st[k].ops = ar.put(g[k]);
-      lv.st[k].small = ar.put(sm[k]);
-      lv.st[k].big = ar.put(bg[k]);
-      lv.st[k].nsmall = (int)sm[k].size();
-      lv.st[k].nbig = (int)bg[k].size();
+      for (int c = 0; c < 4; ++c) {
+        lv.st[k].map[c] = ar.put(maps[k][c]);
+        lv.st[k].nmap[c] = (int)maps[k][c].size();
+      }
     }
     scratch_elems = std::max(scratch_elems, off);
     levels.push_back(lv);
@@ -335,7 +343,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     std::vector<int> row_op;
     std::vector<findgb::InvOp> inv;
     std::vector<findgb::GemmOp> g[2];
-    std::vector<int> sm[2], bg[2];
+    std::vector<int> maps[2][4];
     std::vector<findgb::ExtractOp> ext;
     int64_t off = 0;
     for (const auto& op : p.leaf_ops) {
@@ -385,14 +393,15 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         q.A = M + (int64_t)op.nb * n; q.lda = n; q.sa = slot;
         q.B = Sg; q.ldb = n; q.sb = slot;
         q.D = P; q.ldd = n; q.sd = slot;
-        gemm_ok(q); add_gemm(q, g[0], sm[0], bg[0], &lv.st[0]);
+        const bool c64 = mixed && p.cl[op.cluster].depth > top_levels;
+        gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], c64);
         // Q = P G_K^H = G<_K(C, :)
         q = gemm0();
         q.m = op.c; q.n = n; q.k = n;
         q.A = P; q.lda = n; q.sa = slot;
         q.B = M; q.ldb = n; q.sb = slot; q.opb = 1;
         q.D = Q; q.ldd = n; q.sd = slot;
-        gemm_ok(q); add_gemm(q, g[1], sm[1], bg[1], &lv.st[1]);
+        gemm_ok(q); add_gemm(q, g[1], maps[1], &lv.st[1], c64);
       }
       findgb::ExtractOp x;
       x.K = M;
@@ -411,10 +420,10 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     lv.nstages = lesser ? 2 : 0;
     for (int k = 0; k < lv.nstages; ++k) {
       lv.st[k].ops = ar.put(g[k]);
-      lv.st[k].small = ar.put(sm[k]);
-      lv.st[k].big = ar.put(bg[k]);
-      lv.st[k].nsmall = (int)sm[k].size();
-      lv.st[k].nbig = (int)bg[k].size();
+      for (int c = 0; c < 4; ++c) {
+        lv.st[k].map[c] = ar.put(maps[k][c]);
+        lv.st[k].nmap[c] = (int)maps[k][c].size();
+      }
     }
     scratch_elems = std::max(scratch_elems, off);
     levels.push_back(lv);
@@ -545,8 +554,11 @@ const T* at(const find_handle* h, size_t off) {
   return reinterpret_cast<const T*>(h->ws + h->lay.meta + off);
 }
 
-const int kClasses = 8;
-const char* kClassNames[kClasses] = {"lead", "assemble", "invert", "lu", "trsm", "zgemm32", "zgemm64", "extract"};
+const int kClasses = 10;
+const char* kClassNames[kClasses] = {"lead",    "assemble", "invert",  "lu",      "trsm",
+                                     "zgemm32", "zgemm64",  "extract", "cgemm32", "cgemm64"};
+// profiler class of each GEMM launch class [FP64 small, FP64 big, c64 small, c64 big]
+const int kGemmClass[4] = {5, 6, 8, 9};
 
 cudaEvent_t take_event(find_handle* h) {
   if (!h->ev_free.empty()) {
@@ -601,12 +613,11 @@ void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, boo
   for (int k = 0; k < lv.nstages; ++k) {
     const Stage& s = lv.st[k];
     const findgb::GemmOp* ops = at<findgb::GemmOp>(h, s.ops);
-    if (s.nsmall)
-      timed(h, st, 5, s.fl_small * nb, 0.0,
-            [&] { findgb::launch_gemm(ops, at<int>(h, s.small), s.nsmall, 0, nb, st); });
-    if (s.nbig)
-      timed(h, st, 6, s.fl_big * nb, 0.0,
-            [&] { findgb::launch_gemm(ops, at<int>(h, s.big), s.nbig, 1, nb, st); });
+    for (int c = 0; c < 4; ++c)
+      if (s.nmap[c])
+        timed(h, st, kGemmClass[c], s.fl[c] * nb, 0.0, [&] {
+          findgb::launch_gemm(ops, at<int>(h, s.map[c]), s.nmap[c], c & 1, nb, st, c >> 1);
+        });
   }
   if (lv.leaf)
     timed(h, st, 7, 0.0, lv.by_ext * nb, [&] {
@@ -780,8 +791,9 @@ void run_level_static(find_handle* h, const StaticView& sv, const Level& lv,
   for (int k = 0; k < lv.nstages; ++k) {
     const Stage& s = lv.st[k];
     auto ops = reinterpret_cast<const findgb::GemmOp*>(meta(s.ops));
-    findgb::launch_gemm(ops, reinterpret_cast<const int*>(meta(s.small)), s.nsmall, 0, nb, st);
-    findgb::launch_gemm(ops, reinterpret_cast<const int*>(meta(s.big)), s.nbig, 1, nb, st);
+    for (int c = 0; c < 4; ++c)
+      findgb::launch_gemm(ops, reinterpret_cast<const int*>(meta(s.map[c])), s.nmap[c], c & 1, nb, st,
+                          c >> 1);
   }
   if (lv.leaf)
     findgb::launch_extract(reinterpret_cast<const findgb::ExtractOp*>(meta(lv.ext)), lv.nops,
@@ -922,7 +934,8 @@ extern "C" {
 int find_create(const find_desc* d, find_handle** out) {
   if (!d || !out) return fail(nullptr, FIND_EINVAL, "null descriptor or output");
   *out = nullptr;
-  if (d->precision != FIND_FP64) return fail(nullptr, FIND_EINVAL, "only FIND_FP64 is supported");
+  if (d->precision != FIND_FP64 && d->precision != FIND_MIXED)
+    return fail(nullptr, FIND_EINVAL, "precision must be FIND_FP64 or FIND_MIXED");
   if (d->stencil != 5 && d->stencil != 9) return fail(nullptr, FIND_EINVAL, "stencil must be 5 or 9");
   if (d->max_batch < 0) return fail(nullptr, FIND_EINVAL, "max_batch < 0");
   find_handle* h = new (std::nothrow) find_handle();

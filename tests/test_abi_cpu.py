@@ -118,8 +118,9 @@ def test_workspace_grows_linearly_with_batch(F):
 def test_descriptor_tables_stay_in_bounds(F, nx, ny, stencil, leaf):
     # every operand of every kernel launch lies inside the workspace, for
     # several batch sizes, in both the diag and the lesser configuration
-    f = F.Find(nx, ny, stencil, 1.0, 0.2, leaf=leaf)
-    for batch in (1, 3, 8):
-        for lesser in (False, True):
-            assert f.workspace_bytes(batch, lesser) > 0
-    f.close()
+    for precision in ("fp64", "mixed"):
+        f = F.Find(nx, ny, stencil, 1.0, 0.2, leaf=leaf, precision=precision)
+        for batch in (1, 3, 8):
+            for lesser in (False, True):
+                assert f.workspace_bytes(batch, lesser) > 0
+        f.close()
