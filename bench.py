@@ -121,11 +121,6 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def step_energies(Es, step, rank, world, batch):
-    idx = ((step * world + rank) * batch + np.arange(batch)) % len(Es)
-    return np.ascontiguousarray(Es[idx])
-
-
 def cpu_baseline(mesh, Es):
     """The oracle (O-find) as it stands on one energy point of the workload."""
     from oracle import find as ofind, problem
@@ -180,6 +175,7 @@ def main():
     device = local
     torch.cuda.set_device(device)
     import paper_1104_0623_gb300 as F
+    from paper_1104_0623_gb300.shard import max_over_ranks, step_energies
 
     mesh, Es = bench_mesh(args.mesh), W.c5_energies()
     B = args.batch
@@ -219,11 +215,7 @@ def main():
     clk = clocks.stop()
     prof = f.profile_read()
     f.profile(False)
-    t = e0.elapsed_time(e1) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
     value = ws * args.steps * B / t
 
     # end-to-end through the C ABI with pinned host buffers (copies inside)
@@ -239,11 +231,7 @@ def main():
         for k in range(args.steps):
             f.solve_lesser(E_host[k], 1.0, 0.0, out=(hG, hGl, hJ), stream=stream.cuda_stream)
         barrier()
-        te = time.perf_counter() - th
-        if ws > 1:
-            tt = torch.tensor([te], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(time.perf_counter() - th, dev)
         e2e = {"value": ws * args.steps * B / te, "unit": UNIT, "h2d_bytes_per_step": B * 16,
                "d2h_bytes_per_step": B * n * 16 * 2 + B * nb * 8}
 
