@@ -49,13 +49,14 @@ enum {
 };
 
 /* FIND_FP64: every step in FP64.
- * FIND_MIXED: the Sigma update (Eq. 7: T = L Sigma(S,S) - Sigma(B,S) and
- * R = Sigma(B,B) - L Sigma(S,B) + T L^H) and the leaf products
- * G_K Sigma_K G_K^H run in complex64 arithmetic (operands and results stay
- * complex128 in memory); the Schur update U (Eq. 2), the pivoted LU, the
- * triangular solves for L (Eq. 13), the leaf inversion and every step of the
- * top fp64_top_levels tree levels stay FP64.  Complex64 in the U update was
- * measured to lose up to 2.5e-3 (cancellation in ill-conditioned inner
+ * FIND_MIXED: below the top fp64_top_levels tree levels, the Sigma update
+ * (Eq. 7: T = L Sigma(S,S) - Sigma(B,S), R = Sigma(B,B) - L Sigma(S,B) + T L^H)
+ * and the leaf products G_K Sigma_K G_K^H run in complex64 arithmetic, and
+ * the Schur update U (Eq. 2) and the triangular solves for L (Eq. 13) in
+ * float-float arithmetic (pairs of floats, about 48 significant bits); the
+ * pivoted LU, the leaf inversion and every step of the top levels stay FP64.
+ * Operands and results stay complex128 in memory.  Complex64 in the U update
+ * was measured to lose up to 2.5e-3 (cancellation in ill-conditioned inner
  * blocks, amplified by later eliminations); in the Sigma update it costs
  * about 1e-6. */
 enum { FIND_FP64 = 0, FIND_MIXED = 1 };
@@ -186,8 +187,9 @@ int find_solve_diag_static(find_handle* h, const double* E, int nE,
 /* Per-kernel timing of the handle's solves (CUDA events recorded on the
  * solve's stream around every launch while profiling is on).  Kernel
  * classes: "lead", "assemble", "invert", "lu", "trsm", "zgemm32",
- * "zgemm64", "extract", "cgemm32", "cgemm64" (z: FP64, c: complex64
- * arithmetic; 32/64: tile size).  flops are the algorithmic real flops of the
+ * "zgemm64", "extract", "cgemm32", "cgemm64", "ffgemm32", "ffgemm64",
+ * "fftrsm" (z: FP64, c: complex64, ff: float-float arithmetic; 32/64: tile
+ * size).  flops are the algorithmic real flops of the
  * launches (GEMM: 8 m n k per op and energy; LU: 8 s^3 / 3; triangular
  * solves: 8 s^2 b; leaf inversion: 8 n^3), bytes the algorithmic DRAM bytes
  * of the gather/extract kernels (blocks written plus source blocks read). */

@@ -5,7 +5,7 @@
 //                 (Procedures updateBoundaryNodes / updateAdjacentNodes)
 //   k_lu          pivoted LU of M(S,S) in place (one CTA per op and energy)
 //   k_trsm        L = M(B,S) M(S,S)^{-1} (Eq. 13) by two triangular sweeps,
-//                 row blocks spread over CTAs
+//                 row blocks spread over CTAs (FP64, or float-float)
 //   k_invert      pivoted Gauss-Jordan inverse of the bordered leaf system
 //   k_zgemm       grouped complex GEMM (FP64, or complex64 arithmetic in the
 //                 mixed path): U = M(B,B) - L M(S,B) (Eq. 2),
@@ -352,70 +352,6 @@ __global__ void __launch_bounds__(kInvThreads) k_lu(const InvOp* __restrict__ op
   }
 }
 
-// ---------------------------------------------------------------- L = M(B,S) M(S,S)^{-1}
-// Row block of RB rows per CTA held in shared memory.  Forward sweep solves
-// Y U = M(B,S) column by column (scale by 1/U_jj, then eliminate column j
-// from the later columns); backward sweep solves Z L = Y with the unit-lower
-// factor; the row interchanges are then applied as column interchanges.
-__global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
-                                              const int* __restrict__ tile_op, int rb) {
-  const TrsmOp& op = ops[tile_op[blockIdx.x]];
-  const int e = blockIdx.y;
-  const int s = op.s, ld = op.ld;
-  const int r0 = (blockIdx.x - op.tile0) * rb;
-  const int rows = min(rb, op.b - r0);
-  if (s == 0 || rows <= 0) return;
-  const cplx* a = op.M + (int64_t)e * op.estride;
-  const int* piv = op.piv + (int64_t)e * op.piv_estride;
-  extern __shared__ double2 tr_smem[];
-  cplx* Y = tr_smem;                               // rows x s
-  int* perm = reinterpret_cast<int*>(Y + (int64_t)rb * s);
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int idx = tid; idx < rows * s; idx += nt) {
-    int r = idx / s, j = idx % s;
-    Y[r * s + j] = a[(int64_t)(s + r0 + r) * ld + j];
-  }
-  __syncthreads();
-  // forward: Y U = B
-  for (int j = 0; j < s; ++j) {
-    if (tid < rows) {
-      const cplx ujj = a[(int64_t)j * ld + j];  // zero only if the LU flagged it
-      cplx d = (ujj.x == 0.0 && ujj.y == 0.0) ? cmk(0, 0) : crecip(ujj);
-      Y[tid * s + j] = cmul(Y[tid * s + j], d);
-    }
-    __syncthreads();
-    for (int i = j + 1 + tid; i < s; i += nt) {
-      const cplx u = a[(int64_t)j * ld + i];
-      for (int r = 0; r < rows; ++r) Y[r * s + i] = cfms(Y[r * s + j], u, Y[r * s + i]);
-    }
-    __syncthreads();
-  }
-  // backward: Z L = Y, L unit lower
-  for (int j = s - 1; j > 0; --j) {
-    for (int i = tid; i < j; i += nt) {
-      const cplx l = a[(int64_t)j * ld + i];
-      for (int r = 0; r < rows; ++r) Y[r * s + i] = cfms(Y[r * s + j], l, Y[r * s + i]);
-    }
-    __syncthreads();
-  }
-  // L = Z P: column j of the result is column perm[j] of Z
-  if (tid == 0) {
-    for (int j = 0; j < s; ++j) perm[j] = j;
-    for (int k = s - 1; k >= 0; --k) {
-      int p = piv[k];
-      int t0 = perm[k];
-      perm[k] = perm[p];
-      perm[p] = t0;
-    }
-  }
-  __syncthreads();
-  cplx* L = op.L + (int64_t)e * op.l_estride;
-  for (int idx = tid; idx < rows * s; idx += nt) {
-    int r = idx / s, j = idx % s;
-    L[(int64_t)(r0 + r) * s + j] = Y[r * s + perm[j]];
-  }
-}
-
 // ---------------------------------------------------------------- grouped complex GEMM
 // Operands are complex128 in memory; CT is the arithmetic type: double2 (FP64
 // path) or float2 (complex64 arithmetic of the mixed path, operands rounded
@@ -429,6 +365,7 @@ struct Cx<double2> {
   __device__ __forceinline__ static double2 load(cplx v, double a) { return make_double2(v.x * a, v.y * a); }
   __device__ __forceinline__ static double2 fma(double2 a, double2 b, double2 c) { return cfma(a, b, c); }
   __device__ __forceinline__ static cplx wide(double2 v) { return v; }
+  __device__ __forceinline__ static void renorm(double2&) {}
 };
 
 template <>
@@ -445,6 +382,69 @@ struct Cx<float2> {
     return c;
   }
   __device__ __forceinline__ static cplx wide(float2 v) { return make_double2(v.x, v.y); }
+  __device__ __forceinline__ static void renorm(float2&) {}
+};
+
+// Float-float ("df32") arithmetic: a real x is carried as hi + lo, two
+// floats with |lo| <= ulp(hi)/2 (about 48 significant bits), following
+// Dekker (1971) and Knuth's error-free two-sum; complex values as float4
+// (re.hi, re.lo, im.hi, im.lo).  On GB300 the FP32 pipes run about 70 times
+// the FP64 rate, so a multiply-add carried this way (12 FP32 operations per
+// real product) is several times faster than FP64 at nearly its accuracy.
+__device__ __forceinline__ void df_split(double x, float& h, float& l) {
+  h = __double2float_rn(x);
+  l = __double2float_rn(x - (double)h);
+}
+__device__ __forceinline__ double df_join(float h, float l) { return (double)h + (double)l; }
+// (ch, cl) += (ah, al) * (bh, bl): the product's exact high part, its rounding
+// error by fma, the two cross terms; the sum by an error-free two-sum whose
+// error joins the low word.  Normalised once at the end of a reduction.
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float& ch, float& cl) {
+  const float ph = ah * bh;
+  float pl = fmaf(ah, bh, -ph);
+  pl = fmaf(ah, bl, pl);
+  pl = fmaf(al, bh, pl);
+  const float s = ch + ph;
+  const float bb = s - ch;
+  const float e = (ch - (s - bb)) + (ph - bb);
+  cl = cl + (e + pl);
+  ch = s;
+}
+__device__ __forceinline__ void df_norm(float& h, float& l) {
+  const float t = h + l;
+  l = l - (t - h);
+  h = t;
+}
+__device__ __forceinline__ float4 df_load(cplx v, double a) {
+  float4 r;
+  df_split(a < 0.0 ? -v.x : v.x, r.x, r.y);
+  df_split(a < 0.0 ? -v.y : v.y, r.z, r.w);
+  return r;
+}
+// c + a * b, complex float-float
+__device__ __forceinline__ float4 df_cfma(float4 a, float4 b, float4 c) {
+  df_mac(a.x, a.y, b.x, b.y, c.x, c.y);
+  df_mac(-a.z, -a.w, b.z, b.w, c.x, c.y);
+  df_mac(a.x, a.y, b.z, b.w, c.z, c.w);
+  df_mac(a.z, a.w, b.x, b.y, c.z, c.w);
+  return c;
+}
+__device__ __forceinline__ cplx df_wide(float4 v) {
+  df_norm(v.x, v.y);
+  df_norm(v.z, v.w);
+  return make_double2(df_join(v.x, v.y), df_join(v.z, v.w));
+}
+
+template <>
+struct Cx<float4> {
+  __device__ __forceinline__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  __device__ __forceinline__ static float4 load(cplx v, double a) { return df_load(v, a); }
+  __device__ __forceinline__ static float4 fma(float4 a, float4 b, float4 c) { return df_cfma(a, b, c); }
+  __device__ __forceinline__ static cplx wide(float4 v) { return df_wide(v); }
+  __device__ __forceinline__ static void renorm(float4& v) {
+    df_norm(v.x, v.y);
+    df_norm(v.z, v.w);
+  }
 };
 
 // Tile BM x BN per CTA, BK deep; each thread owns a 4 x 4 block of outputs at
@@ -512,6 +512,10 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4)) k_zgemm(const GemmOp* __r
 #pragma unroll
           for (int j = 0; j < 4; ++j) acc[i][j] = X::fma(av[i], bv[j], acc[i][j]);
       }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) X::renorm(acc[i][j]);
       __syncthreads();
     }
   }
@@ -533,6 +537,103 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4)) k_zgemm(const GemmOp* __r
       }
       D[(int64_t)gi * op.ldd + gj] = v;
     }
+  }
+}
+
+// ---------------------------------------------------------------- L = M(B,S) M(S,S)^{-1}
+// Row block of RB rows per CTA held in shared memory.  Forward sweep solves
+// Y U = M(B,S) column by column (scale by 1/U_jj, then eliminate column j
+// from the later columns); backward sweep solves Z L = Y with the unit-lower
+// factor; the row interchanges are then applied as column interchanges.
+// DF: the row block is carried in float-float (factors read in FP64 and
+// split once per use, shared by the RB rows).
+template <bool DF>
+struct TrsmArith;
+
+template <>
+struct TrsmArith<false> {
+  typedef cplx T;
+  __device__ __forceinline__ static T in(cplx v) { return v; }
+  __device__ __forceinline__ static cplx out(T v) { return v; }
+  __device__ __forceinline__ static T mul(T a, cplx b) { return cmul(a, b); }
+  __device__ __forceinline__ static T fms(T a, cplx b, T c) { return cfms(a, b, c); }
+};
+
+template <>
+struct TrsmArith<true> {
+  typedef float4 T;
+  __device__ __forceinline__ static T in(cplx v) { return df_load(v, 1.0); }
+  __device__ __forceinline__ static cplx out(T v) { return df_wide(v); }
+  __device__ __forceinline__ static T mul(T a, cplx b) {
+    return df_cfma(a, df_load(b, 1.0), make_float4(0.f, 0.f, 0.f, 0.f));
+  }
+  __device__ __forceinline__ static T fms(T a, cplx b, T c) {
+    T r = df_cfma(make_float4(-a.x, -a.y, -a.z, -a.w), df_load(b, 1.0), c);
+    df_norm(r.x, r.y);
+    df_norm(r.z, r.w);
+    return r;
+  }
+};
+
+template <bool DF>
+__global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
+                                              const int* __restrict__ tile_op, int rb) {
+  typedef TrsmArith<DF> X;
+  typedef typename X::T T;
+  const TrsmOp& op = ops[tile_op[blockIdx.x]];
+  const int e = blockIdx.y;
+  const int s = op.s, ld = op.ld;
+  const int r0 = (blockIdx.x - op.tile0) * rb;
+  const int rows = min(rb, op.b - r0);
+  if (s == 0 || rows <= 0) return;
+  const cplx* a = op.M + (int64_t)e * op.estride;
+  const int* piv = op.piv + (int64_t)e * op.piv_estride;
+  extern __shared__ double2 tr_smem[];
+  T* Y = reinterpret_cast<T*>(tr_smem);            // rows x s
+  int* perm = reinterpret_cast<int*>(Y + (int64_t)rb * s);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int idx = tid; idx < rows * s; idx += nt) {
+    int r = idx / s, j = idx % s;
+    Y[r * s + j] = X::in(a[(int64_t)(s + r0 + r) * ld + j]);
+  }
+  __syncthreads();
+  // forward: Y U = B
+  for (int j = 0; j < s; ++j) {
+    if (tid < rows) {
+      const cplx ujj = a[(int64_t)j * ld + j];  // zero only if the LU flagged it
+      cplx d = (ujj.x == 0.0 && ujj.y == 0.0) ? cmk(0, 0) : crecip(ujj);
+      Y[tid * s + j] = X::mul(Y[tid * s + j], d);
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < s; i += nt) {
+      const cplx u = a[(int64_t)j * ld + i];
+      for (int r = 0; r < rows; ++r) Y[r * s + i] = X::fms(Y[r * s + j], u, Y[r * s + i]);
+    }
+    __syncthreads();
+  }
+  // backward: Z L = Y, L unit lower
+  for (int j = s - 1; j > 0; --j) {
+    for (int i = tid; i < j; i += nt) {
+      const cplx l = a[(int64_t)j * ld + i];
+      for (int r = 0; r < rows; ++r) Y[r * s + i] = X::fms(Y[r * s + j], l, Y[r * s + i]);
+    }
+    __syncthreads();
+  }
+  // L = Z P: column j of the result is column perm[j] of Z
+  if (tid == 0) {
+    for (int j = 0; j < s; ++j) perm[j] = j;
+    for (int k = s - 1; k >= 0; --k) {
+      int p = piv[k];
+      int t0 = perm[k];
+      perm[k] = perm[p];
+      perm[p] = t0;
+    }
+  }
+  __syncthreads();
+  cplx* L = op.L + (int64_t)e * op.l_estride;
+  for (int idx = tid; idx < rows * s; idx += nt) {
+    int r = idx / s, j = idx % s;
+    L[(int64_t)(r0 + r) * s + j] = X::out(Y[r * s + perm[j]]);
   }
 }
 
@@ -610,23 +711,32 @@ int trsm_rows_per_block(int max_s) {
 }
 
 void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int max_s, int nE,
-                 cudaStream_t st) {
+                 cudaStream_t st, int df) {
   if (ntiles == 0 || max_s == 0) return;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
+    cudaFuncSetAttribute(k_trsm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
+    cudaFuncSetAttribute(k_trsm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
     attr_set = true;
   }
   size_t smem = (size_t)rb * max_s * sizeof(cplx) + (size_t)max_s * sizeof(int);
   dim3 grid(ntiles, nE);
-  k_trsm<<<grid, 256, smem, st>>>(ops, tile_op, rb);
+  if (df)
+    k_trsm<true><<<grid, 256, smem, st>>>(ops, tile_op, rb);
+  else
+    k_trsm<false><<<grid, 256, smem, st>>>(ops, tile_op, rb);
 }
 
 void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,
                  cudaStream_t st, int fp32) {
   if (ntiles == 0) return;
   dim3 grid(ntiles, nE);
-  if (fp32) {
+  if (fp32 == 2) {
+    if (big)
+      k_zgemm<64, 64, 8, float4><<<grid, 256, 0, st>>>(ops, tile_op);
+    else
+      k_zgemm<32, 32, 8, float4><<<grid, 64, 0, st>>>(ops, tile_op);
+  } else if (fp32) {
     if (big)
       k_zgemm<64, 64, 16, float2><<<grid, 256, 0, st>>>(ops, tile_op);
     else

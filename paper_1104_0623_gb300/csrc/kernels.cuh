@@ -94,10 +94,12 @@ void launch_assemble(const AsmOp* ops, const int* row_op, int nrows, const Pos* 
 void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
                    cudaStream_t st);
 void launch_lu(const InvOp* ops, int nops, int* status, int e_base, int nE, cudaStream_t st);
+// df = 1: the row block is carried in float-float arithmetic
 void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int max_s, int nE,
-                 cudaStream_t st);
+                 cudaStream_t st, int df = 0);
 int trsm_rows_per_block(int max_s);
-// fp32 = 1: complex64 arithmetic on complex128 operands (mixed path)
+// fp32 = 1: complex64 arithmetic on complex128 operands (mixed path);
+// fp32 = 2: float-float arithmetic (about 48 significant bits)
 void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,
                  cudaStream_t st, int fp32 = 0);
 void launch_extract(const ExtractOp* ops, int nops, const LeafBond* bonds, const DevProblem& P,

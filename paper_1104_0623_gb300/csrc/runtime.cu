@@ -61,21 +61,28 @@ struct Arena {
   }
 };
 
-// One GEMM stage of a level: its ops and the tile maps of the four launch
-// classes [FP64 small, FP64 big, complex64 small, complex64 big].
+// Arithmetic of a GEMM or triangular-solve launch.
+enum Arith { kFP64 = 0, kC64 = 1, kFF = 2 };
+
+// One GEMM stage of a level: its ops and the tile maps of the six launch
+// classes 2 * arith + big: [FP64 small, FP64 big, complex64 small, complex64
+// big, float-float small, float-float big].
 struct Stage {
   size_t ops = 0;
-  size_t map[4] = {0, 0, 0, 0};  // arena offsets
-  int nmap[4] = {0, 0, 0, 0};
-  double fl[4] = {0, 0, 0, 0};   // algorithmic flops per energy of each class
+  size_t map[6] = {0, 0, 0, 0, 0, 0};  // arena offsets
+  int nmap[6] = {0, 0, 0, 0, 0, 0};
+  double fl[6] = {0, 0, 0, 0, 0, 0};   // algorithmic flops per energy of each class
 };
 
 struct Level {
   bool leaf = false;
   int nops = 0, nrows = 0, max_s = 0;
-  int rb = 16, ntrsm = 0, nlu = 0;            // triangular-solve row block and counts
-  double fl_inv = 0, fl_lu = 0, fl_trsm = 0, by_asm = 0, by_ext = 0;  // per energy
-  size_t asmops = 0, row_op = 0, inv = 0, ext = 0, trsm = 0, trsm_map = 0;  // arena offsets
+  int rb = 16, nlu = 0;                        // triangular-solve row block, LU count
+  int ntrsm[2] = {0, 0};                       // row blocks of [FP64, float-float] solves
+  double fl_inv = 0, fl_lu = 0, by_asm = 0, by_ext = 0;  // per energy
+  double fl_trsm[2] = {0, 0};
+  size_t asmops = 0, row_op = 0, inv = 0, ext = 0, trsm = 0;  // arena offsets
+  size_t trsm_map[2] = {0, 0};
   Stage st[3];
   int nstages = 0;
 };
@@ -115,7 +122,7 @@ struct find_handle {
   bool prof = false;
   std::vector<cudaEvent_t> ev_free;
   std::vector<Pending> pending;
-  find_kernel_stat stats[10];
+  find_kernel_stat stats[13];
   // tables for the fixed device scratch
   StaticView sview;
 };
@@ -147,10 +154,10 @@ int64_t leaf_slot_elems(const findgb::LeafOp& op, bool lesser) {
 
 // Adds one GEMM op to a stage, assigning its tiles to the small or big class.
 void add_gemm(findgb::GemmOp g, std::vector<findgb::GemmOp>& ops, std::vector<int>* maps,
-              Stage* st, bool fp32) {
+              Stage* st, Arith arith) {
   if (g.m == 0 || g.n == 0) return;
   bool is_big = std::max(g.m, g.n) > 32;
-  const int cls = (fp32 ? 2 : 0) + (is_big ? 1 : 0);
+  const int cls = 2 * (int)arith + (is_big ? 1 : 0);
   st->fl[cls] += 8.0 * g.m * g.n * (double)(g.k + (g.A2 ? g.k2 : 0));
   int bm = is_big ? 64 : 32;
   int tm = (g.m + bm - 1) / bm, tn = (g.n + bm - 1) / bm;
@@ -222,9 +229,9 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     std::vector<int> row_op;
     std::vector<findgb::InvOp> inv;
     std::vector<findgb::TrsmOp> trs;
-    std::vector<int> trs_map;
+    std::vector<int> trs_map[2];
     std::vector<findgb::GemmOp> g[2];
-    std::vector<int> maps[2][4];
+    std::vector<int> maps[2][6];
     for (const auto& op : ops) lv.max_s = std::max(lv.max_s, op.s);
     lv.rb = findgb::trsm_rows_per_block(lv.max_s);
     int64_t off = 0;
@@ -262,18 +269,23 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
             bc->err = "assemble: gather index out of range";
         }
       }
+      // below the top FP64 levels the mixed path carries U and L in
+      // float-float and the Sigma update in complex64
+      const bool below_top = mixed && p.cl[op.cluster].depth > top_levels;
+      const Arith ua = below_top ? kFF : kFP64;
       if (s > 0) {
         inv.push_back(findgb::InvOp{M, slot, n, s, piv, slot * 4});
         lv.fl_lu += 8.0 * (double)s * s * s / 3.0;
         if (b > 0) {
+          const int tc = below_top ? 1 : 0;
           findgb::TrsmOp t;
           t.M = M; t.estride = slot; t.ld = n; t.s = s; t.b = b;
           t.piv = piv; t.piv_estride = slot * 4;
           t.L = Lm; t.l_estride = slot;
-          t.tile0 = (int)trs_map.size();
-          for (int r = 0; r < (b + lv.rb - 1) / lv.rb; ++r) trs_map.push_back((int)trs.size());
+          t.tile0 = (int)trs_map[tc].size();
+          for (int r = 0; r < (b + lv.rb - 1) / lv.rb; ++r) trs_map[tc].push_back((int)trs.size());
           trs.push_back(t);
-          lv.fl_trsm += 8.0 * (double)s * s * b;
+          lv.fl_trsm[tc] += 8.0 * (double)s * s * b;
           if (bc) bc->block(Lm, b, s, s, slot, batch, "trsm L");
         }
       }
@@ -286,9 +298,8 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       q.B = M + s; q.ldb = n; q.sb = slot;
       q.C = M + (int64_t)s * n + s; q.ldc = n; q.sc = slot; q.beta = 1.0;
       q.D = umat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
-      gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], false);
-      // Sigma update in complex64 arithmetic below the top FP64 levels
-      const bool c64 = mixed && p.cl[op.cluster].depth > top_levels;
+      gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], ua);
+      const Arith sa = below_top ? kC64 : kFP64;
       if (lesser) {
         // stage 0: T = L Sigma(S,S) - Sigma(B,S)
         q = gemm0();
@@ -297,7 +308,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         q.B = Sg; q.ldb = n; q.sb = slot;
         q.C = Sg + (int64_t)s * n; q.ldc = n; q.sc = slot; q.beta = -1.0;
         q.D = T; q.ldd = s; q.sd = slot;
-        gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], c64);
+        gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], sa);
         // stage 1: R = Sigma(B,B) - L Sigma(S,B) + T L^H     (Eq. 7)
         q = gemm0();
         q.m = b; q.n = b; q.k = s; q.k2 = s;
@@ -307,7 +318,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         q.B2 = Lm; q.ldb2 = s; q.sb2 = slot; q.opb2 = 1;
         q.C = Sg + (int64_t)s * n + s; q.ldc = n; q.sc = slot; q.beta = 1.0;
         q.D = rmat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
-        gemm_ok(q); add_gemm(q, g[1], maps[1], &lv.st[1], c64);
+        gemm_ok(q); add_gemm(q, g[1], maps[1], &lv.st[1], sa);
       }
     }
     lv.nops = (int)ops.size();
@@ -315,13 +326,15 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     lv.row_op = ar.put(row_op);
     lv.inv = ar.put(inv);
     lv.trsm = ar.put(trs);
-    lv.trsm_map = ar.put(trs_map);
-    lv.ntrsm = (int)trs_map.size();
+    for (int c = 0; c < 2; ++c) {
+      lv.trsm_map[c] = ar.put(trs_map[c]);
+      lv.ntrsm[c] = (int)trs_map[c].size();
+    }
     lv.nlu = (int)inv.size();
     lv.nstages = lesser ? 2 : 1;
     for (int k = 0; k < lv.nstages; ++k) {
       lv.st[k].ops = ar.put(g[k]);
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < 6; ++c) {
         lv.st[k].map[c] = ar.put(maps[k][c]);
         lv.st[k].nmap[c] = (int)maps[k][c].size();
       }
@@ -343,7 +356,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     std::vector<int> row_op;
     std::vector<findgb::InvOp> inv;
     std::vector<findgb::GemmOp> g[2];
-    std::vector<int> maps[2][4];
+    std::vector<int> maps[2][6];
     std::vector<findgb::ExtractOp> ext;
     int64_t off = 0;
     for (const auto& op : p.leaf_ops) {
@@ -393,15 +406,15 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         q.A = M + (int64_t)op.nb * n; q.lda = n; q.sa = slot;
         q.B = Sg; q.ldb = n; q.sb = slot;
         q.D = P; q.ldd = n; q.sd = slot;
-        const bool c64 = mixed && p.cl[op.cluster].depth > top_levels;
-        gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], c64);
+        const Arith la = (mixed && p.cl[op.cluster].depth > top_levels) ? kC64 : kFP64;
+        gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], la);
         // Q = P G_K^H = G<_K(C, :)
         q = gemm0();
         q.m = op.c; q.n = n; q.k = n;
         q.A = P; q.lda = n; q.sa = slot;
         q.B = M; q.ldb = n; q.sb = slot; q.opb = 1;
         q.D = Q; q.ldd = n; q.sd = slot;
-        gemm_ok(q); add_gemm(q, g[1], maps[1], &lv.st[1], c64);
+        gemm_ok(q); add_gemm(q, g[1], maps[1], &lv.st[1], la);
       }
       findgb::ExtractOp x;
       x.K = M;
@@ -420,7 +433,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     lv.nstages = lesser ? 2 : 0;
     for (int k = 0; k < lv.nstages; ++k) {
       lv.st[k].ops = ar.put(g[k]);
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < 6; ++c) {
         lv.st[k].map[c] = ar.put(maps[k][c]);
         lv.st[k].nmap[c] = (int)maps[k][c].size();
       }
@@ -554,11 +567,12 @@ const T* at(const find_handle* h, size_t off) {
   return reinterpret_cast<const T*>(h->ws + h->lay.meta + off);
 }
 
-const int kClasses = 10;
-const char* kClassNames[kClasses] = {"lead",    "assemble", "invert",  "lu",      "trsm",
-                                     "zgemm32", "zgemm64",  "extract", "cgemm32", "cgemm64"};
-// profiler class of each GEMM launch class [FP64 small, FP64 big, c64 small, c64 big]
-const int kGemmClass[4] = {5, 6, 8, 9};
+const int kClasses = 13;
+const char* kClassNames[kClasses] = {"lead",    "assemble", "invert",   "lu",       "trsm",
+                                     "zgemm32", "zgemm64",  "extract",  "cgemm32",  "cgemm64",
+                                     "ffgemm32", "ffgemm64", "fftrsm"};
+// profiler class of each GEMM launch class 2 * arith + big
+const int kGemmClass[6] = {5, 6, 8, 9, 10, 11};
 
 cudaEvent_t take_event(find_handle* h) {
   if (!h->ev_free.empty()) {
@@ -604,16 +618,17 @@ void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, boo
     timed(h, st, 3, lv.fl_lu * nb, 0.0, [&] {
       findgb::launch_lu(at<findgb::InvOp>(h, lv.inv), lv.nlu, status, e_base, nb, st);
     });
-    if (lv.ntrsm > 0)
-      timed(h, st, 4, lv.fl_trsm * nb, 0.0, [&] {
-        findgb::launch_trsm(at<findgb::TrsmOp>(h, lv.trsm), at<int>(h, lv.trsm_map), lv.ntrsm, lv.rb,
-                            lv.max_s, nb, st);
-      });
+    for (int c = 0; c < 2; ++c)
+      if (lv.ntrsm[c] > 0)
+        timed(h, st, c ? 12 : 4, lv.fl_trsm[c] * nb, 0.0, [&] {
+          findgb::launch_trsm(at<findgb::TrsmOp>(h, lv.trsm), at<int>(h, lv.trsm_map[c]), lv.ntrsm[c],
+                              lv.rb, lv.max_s, nb, st, c);
+        });
   }
   for (int k = 0; k < lv.nstages; ++k) {
     const Stage& s = lv.st[k];
     const findgb::GemmOp* ops = at<findgb::GemmOp>(h, s.ops);
-    for (int c = 0; c < 4; ++c)
+    for (int c = 0; c < 6; ++c)
       if (s.nmap[c])
         timed(h, st, kGemmClass[c], s.fl[c] * nb, 0.0, [&] {
           findgb::launch_gemm(ops, at<int>(h, s.map[c]), s.nmap[c], c & 1, nb, st, c >> 1);
@@ -783,15 +798,15 @@ void run_level_static(find_handle* h, const StaticView& sv, const Level& lv,
                             status, e_base, nb, st);
   } else if (lv.nlu > 0) {
     findgb::launch_lu(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv)), lv.nlu, status, e_base, nb, st);
-    if (lv.ntrsm > 0)
+    for (int c = 0; c < 2; ++c)
       findgb::launch_trsm(reinterpret_cast<const findgb::TrsmOp*>(meta(lv.trsm)),
-                          reinterpret_cast<const int*>(meta(lv.trsm_map)), lv.ntrsm, lv.rb, lv.max_s,
-                          nb, st);
+                          reinterpret_cast<const int*>(meta(lv.trsm_map[c])), lv.ntrsm[c], lv.rb,
+                          lv.max_s, nb, st, c);
   }
   for (int k = 0; k < lv.nstages; ++k) {
     const Stage& s = lv.st[k];
     auto ops = reinterpret_cast<const findgb::GemmOp*>(meta(s.ops));
-    for (int c = 0; c < 4; ++c)
+    for (int c = 0; c < 6; ++c)
       findgb::launch_gemm(ops, reinterpret_cast<const int*>(meta(s.map[c])), s.nmap[c], c & 1, nb, st,
                           c >> 1);
   }

@@ -1,7 +1,8 @@
-"""Mixed path (FIND_MIXED): the Sigma update and the leaf G< products in
-complex64 arithmetic, everything feeding U in FP64.  Bar: 1e-5 normwise per
-energy against the FP64 oracle for diag G< (diag G is untouched: it must equal
-the FP64 path bit for bit)."""
+"""Mixed path (FIND_MIXED): below the top FP64 levels the Sigma update and
+the leaf G< products run in complex64, the Schur update U and the solves for
+L in float-float (about 48 significant bits); LU and leaf inversion in FP64.
+Bar: 1e-5 normwise per energy against the FP64 oracle for diag G and diag G<
+(diag G, fed only by float-float and FP64 steps, is held to 1e-9)."""
 
 import numpy as np
 import pytest
@@ -41,15 +42,13 @@ def solve(F, mesh, Es, precision, leaf=8, top=2, max_batch=0):
 def test_c2_mixed_all_energies_within_1e5(F):
     mesh, Es = W.c2(), W.c2_energies()
     G, Gl, J = solve(F, mesh, Es, "mixed", leaf=5)
-    G64, Gl64, J64 = solve(F, mesh, Es, "fp64", leaf=5)
-    assert np.array_equal(G, G64)
     P = problem.MeshProblem.from_mesh(mesh)
     worst = 0.0
     for k in range(0, 64, 4):
         A, Sl = P.assemble(Es[k])
         rG, rGl, rJ, _, _ = dense.dense_outputs(A, Sl, P.H, mesh.nx, mesh.ny, mesh.stencil)
         worst = max(worst, rel(Gl[k], rGl), rel(J[k], rJ.real))
-        assert rel(G[k], rG) <= 1e-10
+        assert rel(G[k], rG) <= 1e-9
     assert worst <= TOL_MIXED, worst
 
 
@@ -64,7 +63,7 @@ def test_mixed_9pt_mesh_against_oracle_find(F, top, tol):
     P = problem.MeshProblem.from_mesh(mesh)
     for k, E in enumerate(Es):
         rG, rGl, _, _ = ofind.find_outputs(P, E, leaf=8, bonds=False)
-        assert rel(G[k], rG) <= 1e-10
+        assert rel(G[k], rG) <= 1e-9
         assert rel(Gl[k], rGl) <= tol, (E, rel(Gl[k], rGl))
 
 
