@@ -58,8 +58,11 @@ enum {
  * Operands and results stay complex128 in memory.  Complex64 in the U update
  * was measured to lose up to 2.5e-3 (cancellation in ill-conditioned inner
  * blocks, amplified by later eliminations); in the Sigma update it costs
- * about 1e-6. */
-enum { FIND_FP64 = 0, FIND_MIXED = 1 };
+ * about 1e-6.
+ * FIND_MIXED_FF: as FIND_MIXED, and below the top levels the pivoted LU and
+ * the leaf inversion run in float-float arithmetic too (only the top levels
+ * stay FP64). */
+enum { FIND_FP64 = 0, FIND_MIXED = 1, FIND_MIXED_FF = 2 };
 
 typedef struct find_handle find_handle;
 
@@ -71,13 +74,19 @@ typedef struct {
                                find_create; NULL means V = 0                   */
   double onsite0;           /* clean onsite energy (4t, or 4t + 4tp for 9)     */
   int leaf;                 /* leaf clusters have both sides <= leaf; 0 = 8    */
-  int precision;            /* FIND_FP64 or FIND_MIXED                         */
+  int precision;            /* FIND_FP64, FIND_MIXED or FIND_MIXED_FF          */
   int device;               /* CUDA device ordinal                             */
   int max_batch;            /* energies solved together; 0 = chosen from free
                                device memory                                   */
   int fp64_top_levels;      /* FIND_MIXED: tree depths 1..fp64_top_levels (the
                                root's children are depth 1) stay FP64; < 0
                                means the default 2                             */
+  int energy_group;         /* energies per concurrent group within a pass
+                               (groups run on their own streams, up to 4);
+                               0 = 8                                           */
+  int invert_smem;          /* bordered leaf systems up to this size are
+                               inverted in shared memory (at most 112);
+                               <= 0 = never (the default: measured slower)     */
 } find_desc;
 
 /* Host-side facts of the plan (no GPU needed). */
@@ -188,8 +197,8 @@ int find_solve_diag_static(find_handle* h, const double* E, int nE,
  * solve's stream around every launch while profiling is on).  Kernel
  * classes: "lead", "assemble", "invert", "lu", "trsm", "zgemm32",
  * "zgemm64", "extract", "cgemm32", "cgemm64", "ffgemm32", "ffgemm64",
- * "fftrsm" (z: FP64, c: complex64, ff: float-float arithmetic; 32/64: tile
- * size).  flops are the algorithmic real flops of the
+ * "fftrsm", "fflu", "ffinvert" (z: FP64, c: complex64, ff: float-float
+ * arithmetic; 32/64: tile size).  flops are the algorithmic real flops of the
  * launches (GEMM: 8 m n k per op and energy; LU: 8 s^3 / 3; triangular
  * solves: 8 s^2 b; leaf inversion: 8 n^3), bytes the algorithmic DRAM bytes
  * of the gather/extract kernels (blocks written plus source blocks read). */

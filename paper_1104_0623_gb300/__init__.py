@@ -18,7 +18,7 @@ import ctypes
 import numpy as np
 
 from . import _abi
-from ._abi import (FIND_FP64, FIND_MIXED, FindError, find_create, find_destroy, find_last_error,  # noqa: F401
+from ._abi import (FIND_FP64, FIND_MIXED, FIND_MIXED_FF, FindError, find_create, find_destroy, find_last_error,  # noqa: F401
                    find_plan_info, find_profile, find_profile_read, find_solve_diag,
                    find_solve_lesser, find_workspace_bytes)
 
@@ -46,7 +46,8 @@ class Find:
     """One mesh: plan built at construction, device workspace kept resident."""
 
     def __init__(self, nx, ny, stencil=5, t=1.0, tp=0.0, V=None, onsite0=None, leaf=8,
-                 device=0, max_batch=0, precision="fp64", fp64_top_levels=2):
+                 device=0, max_batch=0, precision="fp64", fp64_top_levels=2, energy_group=0,
+                 invert_smem=0):
         _abi.load()
         self.nx, self.ny, self.stencil = int(nx), int(ny), int(stencil)
         self.n = self.nx * self.ny
@@ -57,11 +58,12 @@ class Find:
         if self._V is not None and self._V.size != self.n:
             raise ValueError("V must have nx*ny entries")
         self.device = int(device)
-        prec = {"fp64": FIND_FP64, "mixed": FIND_MIXED}[precision]
+        prec = {"fp64": FIND_FP64, "mixed": FIND_MIXED, "mixed_ff": FIND_MIXED_FF}[precision]
         self.precision = precision
         d = _abi.find_desc(self.nx, self.ny, self.stencil, self.t, self.tp,
                            None if self._V is None else self._V.ctypes.data, float(onsite0),
-                           int(leaf), prec, self.device, int(max_batch), int(fp64_top_levels))
+                           int(leaf), prec, self.device, int(max_batch), int(fp64_top_levels),
+                           int(energy_group), int(invert_smem))
         self.handle = find_create(d)
         self.stats = find_plan_info(self.handle)
         self.n_bonds = self.stats.n_bonds

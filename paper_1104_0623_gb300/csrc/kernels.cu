@@ -3,10 +3,13 @@
 //   k_lead_modes / k_lead_dense  lead self-energy closed form (per energy)
 //   k_assemble    gather M = [U_1 A_12; A_21 U_2] (and Sigma_M) ordered [S, B]
 //                 (Procedures updateBoundaryNodes / updateAdjacentNodes)
-//   k_lu          pivoted LU of M(S,S) in place (one CTA per op and energy)
+//   k_lu          pivoted LU of M(S,S) in place (one CTA per op and energy;
+//                 FP64 or float-float)
 //   k_trsm        L = M(B,S) M(S,S)^{-1} (Eq. 13) by two triangular sweeps,
 //                 row blocks spread over CTAs (FP64, or float-float)
 //   k_invert      pivoted Gauss-Jordan inverse of the bordered leaf system
+//                 (in global memory, or held in shared memory when it fits;
+//                 FP64 or float-float)
 //   k_zgemm       grouped complex GEMM (FP64, or complex64 arithmetic in the
 //                 mixed path): U = M(B,B) - L M(S,B) (Eq. 2),
 //                 R = Sigma(B,B) - L Sigma(S,B) + (L Sigma(S,S) - Sigma(B,S)) L^H
@@ -16,6 +19,7 @@
 
 #include <cfloat>
 #include <climits>
+#include <type_traits>
 
 namespace findgb {
 
@@ -63,6 +67,56 @@ __device__ __forceinline__ cplx csqrt_principal(cplx z) {
   double t = sqrt(0.5 * (r + fabs(z.x)));
   if (z.x >= 0.0) return cmk(t, z.y / (2.0 * t));
   return cmk(fabs(z.y) / (2.0 * t), copysign(t, z.y));
+}
+
+// Float-float ("df32") arithmetic: a real x is carried as hi + lo, two
+// floats with |lo| <= ulp(hi)/2 (about 48 significant bits), following
+// Dekker (1971) and Knuth's error-free two-sum; complex values as float4
+// (re.hi, re.lo, im.hi, im.lo).  On GB300 the FP32 pipes run about 70 times
+// the FP64 rate, so a multiply-add carried this way (12 FP32 operations per
+// real product) is several times faster than FP64 at nearly its accuracy.
+__device__ __forceinline__ void df_split(double x, float& h, float& l) {
+  h = __double2float_rn(x);
+  l = __double2float_rn(x - (double)h);
+}
+__device__ __forceinline__ double df_join(float h, float l) { return (double)h + (double)l; }
+// (ch, cl) += (ah, al) * (bh, bl): the product's exact high part, its rounding
+// error by fma, the two cross terms; the sum by an error-free two-sum whose
+// error joins the low word.  Normalised once at the end of a reduction.
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float& ch, float& cl) {
+  const float ph = ah * bh;
+  float pl = fmaf(ah, bh, -ph);
+  pl = fmaf(ah, bl, pl);
+  pl = fmaf(al, bh, pl);
+  const float s = ch + ph;
+  const float bb = s - ch;
+  const float e = (ch - (s - bb)) + (ph - bb);
+  cl = cl + (e + pl);
+  ch = s;
+}
+__device__ __forceinline__ void df_norm(float& h, float& l) {
+  const float t = h + l;
+  l = l - (t - h);
+  h = t;
+}
+__device__ __forceinline__ float4 df_load(cplx v, double a) {
+  float4 r;
+  df_split(a < 0.0 ? -v.x : v.x, r.x, r.y);
+  df_split(a < 0.0 ? -v.y : v.y, r.z, r.w);
+  return r;
+}
+// c + a * b, complex float-float
+__device__ __forceinline__ float4 df_cfma(float4 a, float4 b, float4 c) {
+  df_mac(a.x, a.y, b.x, b.y, c.x, c.y);
+  df_mac(-a.z, -a.w, b.z, b.w, c.x, c.y);
+  df_mac(a.x, a.y, b.z, b.w, c.z, c.w);
+  df_mac(a.z, a.w, b.x, b.y, c.z, c.w);
+  return c;
+}
+__device__ __forceinline__ cplx df_wide(float4 v) {
+  df_norm(v.x, v.y);
+  df_norm(v.z, v.w);
+  return make_double2(df_join(v.x, v.y), df_join(v.z, v.w));
 }
 
 // ---------------------------------------------------------------- lead self-energy
@@ -139,8 +193,8 @@ __device__ __forceinline__ cplx s_orig(const DevProblem& P, int e, int i, int j)
 __global__ void __launch_bounds__(256) k_assemble(const AsmOp* __restrict__ ops,
                                                   const int* __restrict__ row_op,
                                                   const Pos* __restrict__ pos, DevProblem P,
-                                                  int lesser) {
-  const int r = blockIdx.x, e = blockIdx.y;
+                                                  int lesser, int e_off) {
+  const int r = blockIdx.x, e = blockIdx.y + e_off;
   const AsmOp& op = ops[row_op[r]];
   const int n = op.n;
   const int p = r - op.row0;
@@ -171,90 +225,129 @@ __global__ void __launch_bounds__(256) k_assemble(const AsmOp* __restrict__ ops,
   }
 }
 
-// ---------------------------------------------------------------- inversion
-// Gauss-Jordan with partial pivoting (largest |re| + |im|, first index on
-// ties), in place; one CTA per (op, energy).  An exactly zero pivot records
-// the energy in *status and continues with a zero reciprocal.
-constexpr int kInvThreads = 512;
+// ---------------------------------------------------------------- arithmetic of the
+// in-place factorisations.  FP64: entries stay complex128.  Float-float: the
+// kernel rewrites its block in place as (re.hi, re.lo, im.hi, im.lo) floats
+// (the same 16 bytes per entry), works on that, and writes complex128 back at
+// the end.  Pivot magnitudes use |re| + |im| (high words for float-float);
+// pivot reciprocals are taken in FP64 (Smith) and split.
+template <bool DF>
+struct GA;
 
-__global__ void __launch_bounds__(kInvThreads) k_invert(const InvOp* __restrict__ ops,
-                                                        int* __restrict__ status, int e_base) {
-  const InvOp op = ops[blockIdx.x];
-  const int e = blockIdx.y;
-  const int s = op.s, ld = op.ld;
-  if (s == 0) return;
-  cplx* a = op.M + (int64_t)e * op.estride;
-  extern __shared__ double2 inv_smem[];
-  cplx* colk = inv_smem;
-  cplx* rowk = colk + s;
-  int* piv = reinterpret_cast<int*>(rowk + s);
-  __shared__ double red_v[32];
-  __shared__ int red_i[32];
-  __shared__ int sh_p;
+template <>
+struct GA<false> {
+  typedef cplx T;
+  __device__ __forceinline__ static T from(cplx v) { return v; }
+  __device__ __forceinline__ static cplx to(T v) { return v; }
+  __device__ __forceinline__ static double mag(T v) { return fabs(v.x) + fabs(v.y); }
+  __device__ __forceinline__ static T zero() { return cmk(0, 0); }
+  __device__ __forceinline__ static T scale(T a, cplx b) { return cmul(a, b); }
+  __device__ __forceinline__ static T fms(T f, T r, T v) { return cfms(f, r, v); }
+  __device__ __forceinline__ static bool is_zero(T v) { return v.x == 0.0 && v.y == 0.0; }
+};
+
+template <>
+struct GA<true> {
+  typedef float4 T;
+  __device__ __forceinline__ static T from(cplx v) { return df_load(v, 1.0); }
+  __device__ __forceinline__ static cplx to(T v) { return df_wide(v); }
+  __device__ __forceinline__ static double mag(T v) { return fabs((double)v.x) + fabs((double)v.z); }
+  __device__ __forceinline__ static T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  __device__ __forceinline__ static T scale(T a, cplx b) {
+    T r = df_cfma(a, df_load(b, 1.0), make_float4(0.f, 0.f, 0.f, 0.f));
+    df_norm(r.x, r.y);
+    df_norm(r.z, r.w);
+    return r;
+  }
+  __device__ __forceinline__ static T fms(T f, T r, T v) {
+    T o = df_cfma(make_float4(-f.x, -f.y, -f.z, -f.w), r, v);
+    df_norm(o.x, o.y);
+    df_norm(o.z, o.w);
+    return o;
+  }
+  __device__ __forceinline__ static bool is_zero(T v) { return v.x == 0.f && v.z == 0.f; }
+};
+
+// Block-wide argmax of mag over rows k..s-1 of column k (largest magnitude,
+// first index on ties); returns the row.
+template <class X, class T>
+__device__ __forceinline__ int pivot_row(const T* a, int ld, int k, int s, double* red_v, int* red_i,
+                                         int* sh_p) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-
-  for (int k = 0; k < s; ++k) {
-    // pivot search in column k, rows k..s-1
-    double best = -1.0;
-    int bi = INT_MAX;
-    for (int i = k + tid; i < s; i += blockDim.x) {
-      cplx v = a[(int64_t)i * ld + k];
-      double mg = fabs(v.x) + fabs(v.y);
-      if (mg > best) { best = mg; bi = i; }
-    }
+  double best = -1.0;
+  int bi = INT_MAX;
+  for (int i = k + tid; i < s; i += blockDim.x) {
+    double mg = X::mag(a[(int64_t)i * ld + k]);
+    if (mg > best) { best = mg; bi = i; }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    double ob = __shfl_down_sync(0xffffffffu, best, off);
+    int oi = __shfl_down_sync(0xffffffffu, bi, off);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+  __syncthreads();
+  if (warp == 0) {
+    best = lane < nwarp ? red_v[lane] : -1.0;
+    bi = lane < nwarp ? red_i[lane] : INT_MAX;
     for (int off = 16; off > 0; off >>= 1) {
       double ob = __shfl_down_sync(0xffffffffu, best, off);
       int oi = __shfl_down_sync(0xffffffffu, bi, off);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
-    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
-    __syncthreads();
-    if (warp == 0) {
-      best = lane < nwarp ? red_v[lane] : -1.0;
-      bi = lane < nwarp ? red_i[lane] : INT_MAX;
-      for (int off = 16; off > 0; off >>= 1) {
-        double ob = __shfl_down_sync(0xffffffffu, best, off);
-        int oi = __shfl_down_sync(0xffffffffu, bi, off);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (lane == 0) {
-        if (bi == INT_MAX) bi = k;
-        sh_p = bi;
-        piv[k] = bi;
-      }
-    }
-    __syncthreads();
-    const int p = sh_p;
+    if (lane == 0) *sh_p = (bi == INT_MAX) ? k : bi;
+  }
+  __syncthreads();
+  return *sh_p;
+}
+
+// ---------------------------------------------------------------- inversion
+// Gauss-Jordan with partial pivoting, in place on the leading s x s block of
+// a (leading dimension ld); colk, rowk: s entries of scratch, piv: s ints.
+// An exactly zero pivot records the energy in *status and continues with a
+// zero reciprocal.
+constexpr int kInvThreads = 512;
+
+template <class X, class T>
+__device__ void gauss_jordan(T* a, int ld, int s, T* colk, T* rowk, int* piv, int* status,
+                             int energy) {
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int sh_p;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  for (int k = 0; k < s; ++k) {
+    const int p = pivot_row<X>(a, ld, k, s, red_v, red_i, &sh_p);
+    if (tid == 0) piv[k] = p;
     if (p != k)
       for (int j = tid; j < s; j += blockDim.x) {
-        cplx t0 = a[(int64_t)k * ld + j];
+        T t0 = a[(int64_t)k * ld + j];
         a[(int64_t)k * ld + j] = a[(int64_t)p * ld + j];
         a[(int64_t)p * ld + j] = t0;
       }
     __syncthreads();
-    cplx pv = a[(int64_t)k * ld + k];
+    const T pv = a[(int64_t)k * ld + k];
     cplx pinv;
-    if (pv.x == 0.0 && pv.y == 0.0) {
+    if (X::is_zero(pv)) {
       pinv = cmk(0, 0);
-      if (tid == 0) atomicMin(status, e_base + e);
+      if (tid == 0) atomicMin(status, energy);
     } else {
-      pinv = crecip(pv);
+      pinv = crecip(X::to(pv));
     }
     __syncthreads();  // every thread has read the pivot before row k changes
     for (int j = tid; j < s; j += blockDim.x) {
-      cplx v = (j == k) ? pinv : cmul(a[(int64_t)k * ld + j], pinv);
+      T v = (j == k) ? X::from(pinv) : X::scale(a[(int64_t)k * ld + j], pinv);
       rowk[j] = v;
       a[(int64_t)k * ld + j] = v;
     }
-    for (int i = tid; i < s; i += blockDim.x) colk[i] = (i == k) ? cmk(0, 0) : a[(int64_t)i * ld + k];
+    for (int i = tid; i < s; i += blockDim.x) colk[i] = (i == k) ? X::zero() : a[(int64_t)i * ld + k];
     __syncthreads();
     for (int i = warp; i < s; i += nwarp) {
       if (i == k) continue;
-      const cplx f = colk[i];
-      cplx* row = a + (int64_t)i * ld;
+      const T f = colk[i];
+      T* row = a + (int64_t)i * ld;
       for (int j = lane; j < s; j += 32) {
-        cplx v = (j == k) ? cmk(0, 0) : row[j];
-        row[j] = cfms(f, rowk[j], v);
+        T v = (j == k) ? X::zero() : row[j];
+        row[j] = X::fms(f, rowk[j], v);
       }
     }
     __syncthreads();
@@ -264,11 +357,89 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(const InvOp* __restrict_
     const int p = piv[k];
     if (p != k)
       for (int i = tid; i < s; i += blockDim.x) {
-        cplx t0 = a[(int64_t)i * ld + k];
+        T t0 = a[(int64_t)i * ld + k];
         a[(int64_t)i * ld + k] = a[(int64_t)i * ld + p];
         a[(int64_t)i * ld + p] = t0;
       }
     __syncthreads();
+  }
+}
+
+// Rewrites the leading s x s block of a complex128 matrix in the storage of
+// arithmetic X (a no-op for FP64), or back.
+template <class X>
+__device__ __forceinline__ void to_work(cplx* a, int ld, int s) {
+  if (!std::is_same<typename X::T, cplx>::value) {
+    for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) {
+      const int i = idx / s, j = idx % s;
+      cplx v = a[(int64_t)i * ld + j];
+      reinterpret_cast<typename X::T*>(a)[(int64_t)i * ld + j] = X::from(v);
+    }
+    __syncthreads();
+  }
+}
+template <class X>
+__device__ __forceinline__ void from_work(cplx* a, int ld, int s) {
+  if (!std::is_same<typename X::T, cplx>::value) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) {
+      const int i = idx / s, j = idx % s;
+      typename X::T v = reinterpret_cast<typename X::T*>(a)[(int64_t)i * ld + j];
+      a[(int64_t)i * ld + j] = X::to(v);
+    }
+  }
+}
+
+// Inversion in global memory, one CTA per (op, energy).
+template <bool DF>
+__global__ void __launch_bounds__(kInvThreads) k_invert(const InvOp* __restrict__ ops,
+                                                        int* __restrict__ status, int e_base,
+                                                        int e_off) {
+  typedef GA<DF> X;
+  typedef typename X::T T;
+  const InvOp op = ops[blockIdx.x];
+  const int e = blockIdx.y + e_off;
+  const int s = op.s, ld = op.ld;
+  if (s == 0) return;
+  cplx* a = op.M + (int64_t)e * op.estride;
+  extern __shared__ double2 inv_smem[];
+  T* colk = reinterpret_cast<T*>(inv_smem);
+  T* rowk = colk + s;
+  int* piv = reinterpret_cast<int*>(rowk + s);
+  to_work<X>(a, ld, s);
+  gauss_jordan<X>(reinterpret_cast<T*>(a), ld, s, colk, rowk, piv, status, e_base + e);
+  from_work<X>(a, ld, s);
+}
+
+// Inversion with the whole block held in shared memory (s <= kInvSmemMax):
+// no global traffic between the load and the store.
+constexpr int kInvSmemMax = 112;
+
+template <bool DF>
+__global__ void __launch_bounds__(kInvThreads) k_invert_smem(const InvOp* __restrict__ ops,
+                                                             int* __restrict__ status, int e_base,
+                                                             int e_off) {
+  typedef GA<DF> X;
+  typedef typename X::T T;
+  const InvOp op = ops[blockIdx.x];
+  const int e = blockIdx.y + e_off;
+  const int s = op.s, ld = op.ld;
+  if (s == 0) return;
+  cplx* g = op.M + (int64_t)e * op.estride;
+  extern __shared__ double2 invs_smem[];
+  T* a = reinterpret_cast<T*>(invs_smem);  // s x s, leading dimension s
+  T* colk = a + (int64_t)s * s;
+  T* rowk = colk + s;
+  int* piv = reinterpret_cast<int*>(rowk + s);
+  for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) {
+    const int i = idx / s, j = idx % s;
+    a[idx] = X::from(g[(int64_t)i * ld + j]);
+  }
+  __syncthreads();
+  gauss_jordan<X>(a, s, s, colk, rowk, piv, status, e_base + e);
+  for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) {
+    const int i = idx / s, j = idx % s;
+    g[(int64_t)i * ld + j] = X::to(a[idx]);
   }
 }
 
@@ -278,78 +449,56 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(const InvOp* __restrict_
 // below the diagonal.  Whole rows are interchanged, LAPACK style; piv[k] is
 // the row exchanged with row k at step k.  One CTA per (op, energy).  An
 // exactly zero pivot records the energy in *status and continues.
+template <bool DF>
 __global__ void __launch_bounds__(kInvThreads) k_lu(const InvOp* __restrict__ ops,
-                                                    int* __restrict__ status, int e_base) {
+                                                    int* __restrict__ status, int e_base,
+                                                    int e_off) {
+  typedef GA<DF> X;
+  typedef typename X::T T;
   const InvOp op = ops[blockIdx.x];
-  const int e = blockIdx.y;
+  const int e = blockIdx.y + e_off;
   const int s = op.s, ld = op.ld;
   if (s == 0) return;
-  cplx* a = op.M + (int64_t)e * op.estride;
+  cplx* g = op.M + (int64_t)e * op.estride;
   int* piv = op.piv + (int64_t)e * op.piv_estride;
   extern __shared__ double2 lu_smem[];
-  cplx* rowk = lu_smem;
+  T* rowk = reinterpret_cast<T*>(lu_smem);
   __shared__ double red_v[32];
   __shared__ int red_i[32];
   __shared__ int sh_p;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-
+  to_work<X>(g, ld, s);
+  T* a = reinterpret_cast<T*>(g);
   for (int k = 0; k < s; ++k) {
-    double best = -1.0;
-    int bi = INT_MAX;
-    for (int i = k + tid; i < s; i += blockDim.x) {
-      cplx v = a[(int64_t)i * ld + k];
-      double mg = fabs(v.x) + fabs(v.y);
-      if (mg > best) { best = mg; bi = i; }
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      double ob = __shfl_down_sync(0xffffffffu, best, off);
-      int oi = __shfl_down_sync(0xffffffffu, bi, off);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
-    __syncthreads();
-    if (warp == 0) {
-      best = lane < nwarp ? red_v[lane] : -1.0;
-      bi = lane < nwarp ? red_i[lane] : INT_MAX;
-      for (int off = 16; off > 0; off >>= 1) {
-        double ob = __shfl_down_sync(0xffffffffu, best, off);
-        int oi = __shfl_down_sync(0xffffffffu, bi, off);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (lane == 0) {
-        if (bi == INT_MAX) bi = k;
-        sh_p = bi;
-        piv[k] = bi;
-      }
-    }
-    __syncthreads();
-    const int p = sh_p;
+    const int p = pivot_row<X>(a, ld, k, s, red_v, red_i, &sh_p);
+    if (tid == 0) piv[k] = p;
     if (p != k)
       for (int j = tid; j < s; j += blockDim.x) {
-        cplx t0 = a[(int64_t)k * ld + j];
+        T t0 = a[(int64_t)k * ld + j];
         a[(int64_t)k * ld + j] = a[(int64_t)p * ld + j];
         a[(int64_t)p * ld + j] = t0;
       }
     __syncthreads();
-    cplx pv = a[(int64_t)k * ld + k];
+    const T pv = a[(int64_t)k * ld + k];
     cplx pinv;
-    if (pv.x == 0.0 && pv.y == 0.0) {
+    if (X::is_zero(pv)) {
       pinv = cmk(0, 0);
       if (tid == 0) atomicMin(status, e_base + e);
     } else {
-      pinv = crecip(pv);
+      pinv = crecip(X::to(pv));
     }
     for (int j = k + 1 + tid; j < s; j += blockDim.x) rowk[j] = a[(int64_t)k * ld + j];
     for (int i = k + 1 + tid; i < s; i += blockDim.x)
-      a[(int64_t)i * ld + k] = cmul(a[(int64_t)i * ld + k], pinv);
+      a[(int64_t)i * ld + k] = X::scale(a[(int64_t)i * ld + k], pinv);
     __syncthreads();
     for (int i = k + 1 + warp; i < s; i += nwarp) {
-      cplx* row = a + (int64_t)i * ld;
-      const cplx l = row[k];
-      for (int j = k + 1 + lane; j < s; j += 32) row[j] = cfms(l, rowk[j], row[j]);
+      T* row = a + (int64_t)i * ld;
+      const T l = row[k];
+      for (int j = k + 1 + lane; j < s; j += 32) row[j] = X::fms(l, rowk[j], row[j]);
     }
     __syncthreads();
   }
+  from_work<X>(g, ld, s);
 }
 
 // ---------------------------------------------------------------- grouped complex GEMM
@@ -385,56 +534,6 @@ struct Cx<float2> {
   __device__ __forceinline__ static void renorm(float2&) {}
 };
 
-// Float-float ("df32") arithmetic: a real x is carried as hi + lo, two
-// floats with |lo| <= ulp(hi)/2 (about 48 significant bits), following
-// Dekker (1971) and Knuth's error-free two-sum; complex values as float4
-// (re.hi, re.lo, im.hi, im.lo).  On GB300 the FP32 pipes run about 70 times
-// the FP64 rate, so a multiply-add carried this way (12 FP32 operations per
-// real product) is several times faster than FP64 at nearly its accuracy.
-__device__ __forceinline__ void df_split(double x, float& h, float& l) {
-  h = __double2float_rn(x);
-  l = __double2float_rn(x - (double)h);
-}
-__device__ __forceinline__ double df_join(float h, float l) { return (double)h + (double)l; }
-// (ch, cl) += (ah, al) * (bh, bl): the product's exact high part, its rounding
-// error by fma, the two cross terms; the sum by an error-free two-sum whose
-// error joins the low word.  Normalised once at the end of a reduction.
-__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float& ch, float& cl) {
-  const float ph = ah * bh;
-  float pl = fmaf(ah, bh, -ph);
-  pl = fmaf(ah, bl, pl);
-  pl = fmaf(al, bh, pl);
-  const float s = ch + ph;
-  const float bb = s - ch;
-  const float e = (ch - (s - bb)) + (ph - bb);
-  cl = cl + (e + pl);
-  ch = s;
-}
-__device__ __forceinline__ void df_norm(float& h, float& l) {
-  const float t = h + l;
-  l = l - (t - h);
-  h = t;
-}
-__device__ __forceinline__ float4 df_load(cplx v, double a) {
-  float4 r;
-  df_split(a < 0.0 ? -v.x : v.x, r.x, r.y);
-  df_split(a < 0.0 ? -v.y : v.y, r.z, r.w);
-  return r;
-}
-// c + a * b, complex float-float
-__device__ __forceinline__ float4 df_cfma(float4 a, float4 b, float4 c) {
-  df_mac(a.x, a.y, b.x, b.y, c.x, c.y);
-  df_mac(-a.z, -a.w, b.z, b.w, c.x, c.y);
-  df_mac(a.x, a.y, b.z, b.w, c.z, c.w);
-  df_mac(a.z, a.w, b.x, b.y, c.z, c.w);
-  return c;
-}
-__device__ __forceinline__ cplx df_wide(float4 v) {
-  df_norm(v.x, v.y);
-  df_norm(v.z, v.w);
-  return make_double2(df_join(v.x, v.y), df_join(v.z, v.w));
-}
-
 template <>
 struct Cx<float4> {
   __device__ __forceinline__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
@@ -451,13 +550,14 @@ struct Cx<float4> {
 // rows ty + i*BM/4, cols tx + j*BN/4.  alpha is folded into the A tile.
 template <int BM, int BN, int BK, class CT>
 __global__ void __launch_bounds__((BM / 4) * (BN / 4)) k_zgemm(const GemmOp* __restrict__ ops,
-                                                               const int* __restrict__ tile_op) {
+                                                               const int* __restrict__ tile_op,
+                                                               int e_off) {
   typedef Cx<CT> X;
   constexpr int NT = (BM / 4) * (BN / 4);
   constexpr int RS = BM / 4, CS = BN / 4;
   __shared__ CT As[BK][BM + 1];
   __shared__ CT Bs[BK][BN + 1];
-  const int t = blockIdx.x, e = blockIdx.y;
+  const int t = blockIdx.x, e = blockIdx.y + e_off;
   const GemmOp& op = ops[tile_op[t]];
   const int local = t - op.tile0;
   const int m0 = (local / op.tiles_n) * BM, n0 = (local % op.tiles_n) * BN;
@@ -577,11 +677,11 @@ struct TrsmArith<true> {
 
 template <bool DF>
 __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
-                                              const int* __restrict__ tile_op, int rb) {
+                                              const int* __restrict__ tile_op, int rb, int e_off) {
   typedef TrsmArith<DF> X;
   typedef typename X::T T;
   const TrsmOp& op = ops[tile_op[blockIdx.x]];
-  const int e = blockIdx.y;
+  const int e = blockIdx.y + e_off;
   const int s = op.s, ld = op.ld;
   const int r0 = (blockIdx.x - op.tile0) * rb;
   const int rows = min(rb, op.b - r0);
@@ -624,6 +724,7 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
     for (int j = 0; j < s; ++j) perm[j] = j;
     for (int k = s - 1; k >= 0; --k) {
       int p = piv[k];
+      if (p < k || p >= s) p = k;  // a valid interchange of step k lies in [k, s)
       int t0 = perm[k];
       perm[k] = perm[p];
       perm[p] = t0;
@@ -642,9 +743,9 @@ __global__ void __launch_bounds__(256) k_extract(const ExtractOp* __restrict__ o
                                                  const LeafBond* __restrict__ bonds, DevProblem P,
                                                  int lesser, int want_bonds, cplx* __restrict__ diagG,
                                                  cplx* __restrict__ diagGl, double* __restrict__ J,
-                                                 int64_t n_nodes, int64_t n_bonds) {
+                                                 int64_t n_nodes, int64_t n_bonds, int e_off) {
   const ExtractOp op = ops[blockIdx.x];
-  const int e = blockIdx.y;
+  const int e = blockIdx.y + e_off;
   const cplx* K = op.K + (int64_t)e * op.estride;
   const cplx* Q = op.Q + (int64_t)e * op.estride;
   for (int i = threadIdx.x; i < op.c; i += blockDim.x) {
@@ -676,31 +777,53 @@ void launch_lead_dense(const cplx* sig_modes, const double* phi, int nx, int nE,
 }
 
 void launch_assemble(const AsmOp* ops, const int* row_op, int nrows, const Pos* pos,
-                     const DevProblem& P, int lesser, int nE, cudaStream_t st) {
+                     const DevProblem& P, int lesser, int nE, cudaStream_t st, int e_off) {
   if (nrows == 0) return;
   dim3 grid(nrows, nE);
-  k_assemble<<<grid, 256, 0, st>>>(ops, row_op, pos, P, lesser);
+  k_assemble<<<grid, 256, 0, st>>>(ops, row_op, pos, P, lesser, e_off);
 }
 
 void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
-                   cudaStream_t st) {
+                   cudaStream_t st, int e_off, int df, int in_smem) {
   if (nops == 0 || max_s == 0) return;
-  size_t smem = (size_t)max_s * (2 * sizeof(cplx) + sizeof(int));
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_invert, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)((size_t)kMaxInvert * (2 * sizeof(cplx) + sizeof(int))));
+    const int glob = (int)((size_t)kMaxInvert * (2 * sizeof(cplx) + sizeof(int)));
+    const int sm = (int)((size_t)kInvSmemMax * kInvSmemMax * sizeof(cplx) +
+                         (size_t)kInvSmemMax * (2 * sizeof(cplx) + sizeof(int)));
+    cudaFuncSetAttribute(k_invert<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, glob);
+    cudaFuncSetAttribute(k_invert<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, glob);
+    cudaFuncSetAttribute(k_invert_smem<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_invert_smem<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     attr_set = true;
   }
   dim3 grid(nops, nE);
-  k_invert<<<grid, kInvThreads, smem, st>>>(ops, status, e_base);
+  if (in_smem) {
+    size_t smem = (size_t)max_s * max_s * sizeof(cplx) + (size_t)max_s * (2 * sizeof(cplx) + sizeof(int));
+    if (df)
+      k_invert_smem<true><<<grid, kInvThreads, smem, st>>>(ops, status, e_base, e_off);
+    else
+      k_invert_smem<false><<<grid, kInvThreads, smem, st>>>(ops, status, e_base, e_off);
+  } else {
+    size_t smem = (size_t)max_s * (2 * sizeof(cplx) + sizeof(int));
+    if (df)
+      k_invert<true><<<grid, kInvThreads, smem, st>>>(ops, status, e_base, e_off);
+    else
+      k_invert<false><<<grid, kInvThreads, smem, st>>>(ops, status, e_base, e_off);
+  }
 }
 
-void launch_lu(const InvOp* ops, int nops, int* status, int e_base, int nE, cudaStream_t st) {
+void launch_lu(const InvOp* ops, int nops, int* status, int e_base, int nE, cudaStream_t st,
+               int e_off, int df) {
   if (nops == 0) return;
   dim3 grid(nops, nE);
-  k_lu<<<grid, kInvThreads, kMaxInvert * sizeof(cplx), st>>>(ops, status, e_base);
+  if (df)
+    k_lu<true><<<grid, kInvThreads, kMaxInvert * sizeof(cplx), st>>>(ops, status, e_base, e_off);
+  else
+    k_lu<false><<<grid, kInvThreads, kMaxInvert * sizeof(cplx), st>>>(ops, status, e_base, e_off);
 }
+
+int invert_smem_max() { return kInvSmemMax; }
 
 constexpr int kTrsmSmem = 196608;
 
@@ -711,7 +834,7 @@ int trsm_rows_per_block(int max_s) {
 }
 
 void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int max_s, int nE,
-                 cudaStream_t st, int df) {
+                 cudaStream_t st, int df, int e_off) {
   if (ntiles == 0 || max_s == 0) return;
   static bool attr_set = false;
   if (!attr_set) {
@@ -722,40 +845,40 @@ void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int 
   size_t smem = (size_t)rb * max_s * sizeof(cplx) + (size_t)max_s * sizeof(int);
   dim3 grid(ntiles, nE);
   if (df)
-    k_trsm<true><<<grid, 256, smem, st>>>(ops, tile_op, rb);
+    k_trsm<true><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
   else
-    k_trsm<false><<<grid, 256, smem, st>>>(ops, tile_op, rb);
+    k_trsm<false><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
 }
 
 void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,
-                 cudaStream_t st, int fp32) {
+                 cudaStream_t st, int fp32, int e_off) {
   if (ntiles == 0) return;
   dim3 grid(ntiles, nE);
   if (fp32 == 2) {
     if (big)
-      k_zgemm<64, 64, 8, float4><<<grid, 256, 0, st>>>(ops, tile_op);
+      k_zgemm<64, 64, 8, float4><<<grid, 256, 0, st>>>(ops, tile_op, e_off);
     else
-      k_zgemm<32, 32, 8, float4><<<grid, 64, 0, st>>>(ops, tile_op);
+      k_zgemm<32, 32, 8, float4><<<grid, 64, 0, st>>>(ops, tile_op, e_off);
   } else if (fp32) {
     if (big)
-      k_zgemm<64, 64, 16, float2><<<grid, 256, 0, st>>>(ops, tile_op);
+      k_zgemm<64, 64, 16, float2><<<grid, 256, 0, st>>>(ops, tile_op, e_off);
     else
-      k_zgemm<32, 32, 16, float2><<<grid, 64, 0, st>>>(ops, tile_op);
+      k_zgemm<32, 32, 16, float2><<<grid, 64, 0, st>>>(ops, tile_op, e_off);
   } else {
     if (big)
-      k_zgemm<64, 64, 8, double2><<<grid, 256, 0, st>>>(ops, tile_op);
+      k_zgemm<64, 64, 8, double2><<<grid, 256, 0, st>>>(ops, tile_op, e_off);
     else
-      k_zgemm<32, 32, 8, double2><<<grid, 64, 0, st>>>(ops, tile_op);
+      k_zgemm<32, 32, 8, double2><<<grid, 64, 0, st>>>(ops, tile_op, e_off);
   }
 }
 
 void launch_extract(const ExtractOp* ops, int nops, const LeafBond* bonds, const DevProblem& P,
                     int lesser, int want_bonds, cplx* diagG, cplx* diagGl, double* J,
-                    int64_t n_nodes, int64_t n_bonds, int nE, cudaStream_t st) {
+                    int64_t n_nodes, int64_t n_bonds, int nE, cudaStream_t st, int e_off) {
   if (nops == 0) return;
   dim3 grid(nops, nE);
   k_extract<<<grid, 256, 0, st>>>(ops, bonds, P, lesser, want_bonds, diagG, diagGl, J, n_nodes,
-                                  n_bonds);
+                                  n_bonds, e_off);
 }
 
 }  // namespace findgb

@@ -89,22 +89,28 @@ void launch_lead_modes(const cplx* E, int nE, const double* eps, const double* t
                        cplx* sig_modes, cudaStream_t st);
 void launch_lead_dense(const cplx* sig_modes, const double* phi, int nx, int nE, cplx* out,
                        cudaStream_t st);
+// Every launch covers energies e_off .. e_off + nE - 1 of the current pass
+// (grid.y = nE); independent energy groups can run on separate streams.
 void launch_assemble(const AsmOp* ops, const int* row_op, int nrows, const Pos* pos,
-                     const DevProblem& P, int lesser, int nE, cudaStream_t st);
+                     const DevProblem& P, int lesser, int nE, cudaStream_t st, int e_off = 0);
+// df = 1: float-float arithmetic; in_smem = 1: the block is held in shared
+// memory (every op of the launch must have s <= invert_smem_max())
 void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
-                   cudaStream_t st);
-void launch_lu(const InvOp* ops, int nops, int* status, int e_base, int nE, cudaStream_t st);
+                   cudaStream_t st, int e_off = 0, int df = 0, int in_smem = 0);
+int invert_smem_max();
+void launch_lu(const InvOp* ops, int nops, int* status, int e_base, int nE, cudaStream_t st,
+               int e_off = 0, int df = 0);
 // df = 1: the row block is carried in float-float arithmetic
 void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int max_s, int nE,
-                 cudaStream_t st, int df = 0);
+                 cudaStream_t st, int df = 0, int e_off = 0);
 int trsm_rows_per_block(int max_s);
 // fp32 = 1: complex64 arithmetic on complex128 operands (mixed path);
 // fp32 = 2: float-float arithmetic (about 48 significant bits)
 void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,
-                 cudaStream_t st, int fp32 = 0);
+                 cudaStream_t st, int fp32 = 0, int e_off = 0);
 void launch_extract(const ExtractOp* ops, int nops, const LeafBond* bonds, const DevProblem& P,
                     int lesser, int want_bonds, cplx* diagG, cplx* diagGl, double* J,
-                    int64_t n_nodes, int64_t n_bonds, int nE, cudaStream_t st);
+                    int64_t n_nodes, int64_t n_bonds, int nE, cudaStream_t st, int e_off = 0);
 
 constexpr int kMaxInvert = 2048;  // largest block the in-CTA inversion accepts
 

@@ -77,12 +77,19 @@ struct Stage {
 struct Level {
   bool leaf = false;
   int nops = 0, nrows = 0, max_s = 0;
-  int rb = 16, nlu = 0;                        // triangular-solve row block, LU count
+  int rb = 16;                                 // triangular-solve row block
   int ntrsm[2] = {0, 0};                       // row blocks of [FP64, float-float] solves
-  double fl_inv = 0, fl_lu = 0, by_asm = 0, by_ext = 0;  // per energy
+  double by_asm = 0, by_ext = 0;               // per energy
   double fl_trsm[2] = {0, 0};
-  size_t asmops = 0, row_op = 0, inv = 0, ext = 0, trsm = 0;  // arena offsets
+  size_t asmops = 0, row_op = 0, ext = 0, trsm = 0;  // arena offsets
   size_t trsm_map[2] = {0, 0};
+  // LU (elimination levels) or inversion (leaf level) ops in four lists,
+  // index df + 2 * in_smem: [FP64, float-float, FP64 in shared memory,
+  // float-float in shared memory]
+  size_t inv[4] = {0, 0, 0, 0};
+  int ninv[4] = {0, 0, 0, 0};
+  int inv_max[4] = {0, 0, 0, 0};
+  double fl_inv[4] = {0, 0, 0, 0};
   Stage st[3];
   int nstages = 0;
 };
@@ -122,9 +129,12 @@ struct find_handle {
   bool prof = false;
   std::vector<cudaEvent_t> ev_free;
   std::vector<Pending> pending;
-  find_kernel_stat stats[13];
+  find_kernel_stat stats[15];
   // tables for the fixed device scratch
   StaticView sview;
+  // streams and events of the concurrent energy groups of one pass
+  std::vector<cudaStream_t> gstreams;
+  std::vector<cudaEvent_t> gevents;
 };
 
 namespace {
@@ -183,6 +193,10 @@ findgb::GemmOp gemm0() {
 struct Bounds {
   const unsigned char* lo = nullptr;
   const unsigned char* hi = nullptr;
+  // the level scratch: energy e owns [s_lo + e * s_stride, s_lo + (e+1) * s_stride)
+  const unsigned char* s_lo = nullptr;
+  const unsigned char* s_hi = nullptr;
+  int64_t s_stride = 0;
   std::string err;
   void block(const cplx* p, int64_t rows, int64_t cols, int64_t ld, int64_t estride, int batch,
              const char* what) {
@@ -191,7 +205,15 @@ struct Bounds {
     const unsigned char* first = reinterpret_cast<const unsigned char*>(p);
     const unsigned char* last = reinterpret_cast<const unsigned char*>(
         p + (rows - 1) * ld + cols + (int64_t)(batch - 1) * estride);
-    if (first < lo || last > hi) err = std::string(what) + ": operand outside the workspace";
+    if (first < lo || last > hi) { err = std::string(what) + ": operand outside the workspace"; return; }
+    if (s_lo && first >= s_lo && first < s_hi) {
+      // a scratch operand: one energy's extent must stay inside that energy's
+      // region, so concurrent energy groups never share scratch
+      const int64_t off = (int64_t)(first - s_lo) % s_stride;
+      const int64_t extent = ((rows - 1) * ld + cols) * (int64_t)sizeof(cplx);
+      if ((int64_t)estride * (int64_t)sizeof(cplx) != s_stride || off + extent > s_stride)
+        err = std::string(what) + ": scratch operand crosses its energy's region";
+    }
   }
 };
 
@@ -207,7 +229,12 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
   auto rmat = [&](int id) { return (id < 0 || !R) ? (cplx*)nullptr : R + p.mat_off[id] * batch; };
   levels.clear();
   scratch_elems = 0;
-  const bool mixed = h->desc.precision == FIND_MIXED;
+  const bool mixed = h->desc.precision == FIND_MIXED || h->desc.precision == FIND_MIXED_FF;
+  const bool ff_all = h->desc.precision == FIND_MIXED_FF;
+  // shared-memory inversion only on request: measured slower than the
+  // global-memory kernel (one 200 KB CTA per SM cannot hide its barriers)
+  const int inv_smem = h->desc.invert_smem <= 0 ? 0
+                       : std::min(h->desc.invert_smem, findgb::invert_smem_max());
   const int top_levels = h->desc.fp64_top_levels < 0 ? 2 : h->desc.fp64_top_levels;
   auto gemm_ok = [&](const findgb::GemmOp& q) {
     if (!bc || q.m == 0 || q.n == 0) return;
@@ -223,11 +250,33 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     bc->block(q.D, q.m, q.n, q.ldd, q.sd, batch, "gemm D");
   };
 
+  // Scratch is energy-major: energy e owns [e * escr, (e + 1) * escr) for
+  // every level, and a level lays its ops out inside that region.  Energy
+  // groups running concurrently on different streams (at different levels)
+  // therefore never touch each other's scratch.
+  int64_t escr = 0;
+  for (const auto& lvops : p.up_levels) {
+    int64_t t = 0;
+    for (const auto& op : lvops) t += op_slot_elems(op, lesser);
+    escr = std::max(escr, t);
+  }
+  for (const auto& lvops : p.dn_levels) {
+    int64_t t = 0;
+    for (const auto& op : lvops) t += op_slot_elems(op, lesser);
+    escr = std::max(escr, t);
+  }
+  {
+    int64_t t = 0;
+    for (const auto& op : p.leaf_ops) t += leaf_slot_elems(op, lesser);
+    escr = std::max(escr, t);
+  }
+  escr = (escr + 15) & ~int64_t(15);  // keep every energy's region 256-byte aligned
+
   auto elim_level = [&](const std::vector<findgb::ElimOp>& ops) {
     Level lv;
     std::vector<findgb::AsmOp> asmops;
     std::vector<int> row_op;
-    std::vector<findgb::InvOp> inv;
+    std::vector<findgb::InvOp> inv[4];
     std::vector<findgb::TrsmOp> trs;
     std::vector<int> trs_map[2];
     std::vector<findgb::GemmOp> g[2];
@@ -237,7 +286,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     int64_t off = 0;
     for (const auto& op : ops) {
       const int64_t slot = op_slot_elems(op, lesser);
-      cplx* M = S0 + off * batch;
+      cplx* M = S0 + off;  // energy e at M + e * escr
       cplx* Sg = M + (int64_t)op.n * op.n;
       cplx* Lm = M + (lesser ? 2 : 1) * (int64_t)op.n * op.n;
       cplx* T = Lm + (int64_t)op.b * op.s;
@@ -251,17 +300,17 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       a.u1 = umat(op.src1); a.r1 = rmat(op.src1); a.d1 = op.src1 < 0 ? 0 : p.mat_dim[op.src1];
       a.u2 = umat(op.src2); a.r2 = rmat(op.src2); a.d2 = op.src2 < 0 ? 0 : p.mat_dim[op.src2];
       a.M = M;
-      a.estride = slot;
+      a.estride = escr;
       for (int r = 0; r < n; ++r) row_op.push_back((int)asmops.size());
       lv.nrows += n;
       asmops.push_back(a);
       if (bc) {
-        bc->block(M, lesser ? 2 * (int64_t)n : n, n, n, slot, batch, "assemble M");
+        bc->block(M, lesser ? 2 * (int64_t)n : n, n, n, escr, batch, "assemble M");
         if (a.u1) bc->block(a.u1, a.d1, a.d1, a.d1, (int64_t)a.d1 * a.d1, batch, "source U1");
         if (a.u2) bc->block(a.u2, a.d2, a.d2, a.d2, (int64_t)a.d2 * a.d2, batch, "source U2");
         if (a.r1) bc->block(a.r1, a.d1, a.d1, a.d1, (int64_t)a.d1 * a.d1, batch, "source R1");
         if (a.r2) bc->block(a.r2, a.d2, a.d2, a.d2, (int64_t)a.d2 * a.d2, batch, "source R2");
-        if (s > 0) bc->block(reinterpret_cast<const cplx*>(piv), 1, (s + 3) / 4, (s + 3) / 4, slot, batch, "pivots");
+        if (s > 0) bc->block(reinterpret_cast<const cplx*>(piv), 1, (s + 3) / 4, (s + 3) / 4, escr, batch, "pivots");
         for (int q = 0; q < n && bc->err.empty(); ++q) {
           const findgb::Pos& pq = p.pos[op.pos + q];
           int d = pq.src == 1 ? a.d1 : pq.src == 2 ? a.d2 : 1;
@@ -274,19 +323,21 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       const bool below_top = mixed && p.cl[op.cluster].depth > top_levels;
       const Arith ua = below_top ? kFF : kFP64;
       if (s > 0) {
-        inv.push_back(findgb::InvOp{M, slot, n, s, piv, slot * 4});
-        lv.fl_lu += 8.0 * (double)s * s * s / 3.0;
+        const int lc = (ff_all && below_top) ? 1 : 0;
+        inv[lc].push_back(findgb::InvOp{M, escr, n, s, piv, escr * 4});
+        lv.inv_max[lc] = std::max(lv.inv_max[lc], s);
+        lv.fl_inv[lc] += 8.0 * (double)s * s * s / 3.0;
         if (b > 0) {
           const int tc = below_top ? 1 : 0;
           findgb::TrsmOp t;
-          t.M = M; t.estride = slot; t.ld = n; t.s = s; t.b = b;
-          t.piv = piv; t.piv_estride = slot * 4;
-          t.L = Lm; t.l_estride = slot;
+          t.M = M; t.estride = escr; t.ld = n; t.s = s; t.b = b;
+          t.piv = piv; t.piv_estride = escr * 4;
+          t.L = Lm; t.l_estride = escr;
           t.tile0 = (int)trs_map[tc].size();
           for (int r = 0; r < (b + lv.rb - 1) / lv.rb; ++r) trs_map[tc].push_back((int)trs.size());
           trs.push_back(t);
           lv.fl_trsm[tc] += 8.0 * (double)s * s * b;
-          if (bc) bc->block(Lm, b, s, s, slot, batch, "trsm L");
+          if (bc) bc->block(Lm, b, s, s, escr, batch, "trsm L");
         }
       }
       lv.by_asm += 16.0 * ((lesser ? 2.0 : 1.0) * n * n +
@@ -294,9 +345,9 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       // stage 0: U = M(B,B) - L M(S,B)                        (Eq. 2)
       findgb::GemmOp q = gemm0();
       q.m = b; q.n = b; q.k = s;
-      q.A = Lm; q.lda = s; q.sa = slot; q.alpha = -1.0;
-      q.B = M + s; q.ldb = n; q.sb = slot;
-      q.C = M + (int64_t)s * n + s; q.ldc = n; q.sc = slot; q.beta = 1.0;
+      q.A = Lm; q.lda = s; q.sa = escr; q.alpha = -1.0;
+      q.B = M + s; q.ldb = n; q.sb = escr;
+      q.C = M + (int64_t)s * n + s; q.ldc = n; q.sc = escr; q.beta = 1.0;
       q.D = umat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
       gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], ua);
       const Arith sa = below_top ? kC64 : kFP64;
@@ -304,19 +355,19 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         // stage 0: T = L Sigma(S,S) - Sigma(B,S)
         q = gemm0();
         q.m = b; q.n = s; q.k = s;
-        q.A = Lm; q.lda = s; q.sa = slot;
-        q.B = Sg; q.ldb = n; q.sb = slot;
-        q.C = Sg + (int64_t)s * n; q.ldc = n; q.sc = slot; q.beta = -1.0;
-        q.D = T; q.ldd = s; q.sd = slot;
+        q.A = Lm; q.lda = s; q.sa = escr;
+        q.B = Sg; q.ldb = n; q.sb = escr;
+        q.C = Sg + (int64_t)s * n; q.ldc = n; q.sc = escr; q.beta = -1.0;
+        q.D = T; q.ldd = s; q.sd = escr;
         gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], sa);
         // stage 1: R = Sigma(B,B) - L Sigma(S,B) + T L^H     (Eq. 7)
         q = gemm0();
         q.m = b; q.n = b; q.k = s; q.k2 = s;
-        q.A = Lm; q.lda = s; q.sa = slot; q.alpha = -1.0;
-        q.B = Sg + s; q.ldb = n; q.sb = slot;
-        q.A2 = T; q.lda2 = s; q.sa2 = slot; q.alpha2 = 1.0;
-        q.B2 = Lm; q.ldb2 = s; q.sb2 = slot; q.opb2 = 1;
-        q.C = Sg + (int64_t)s * n + s; q.ldc = n; q.sc = slot; q.beta = 1.0;
+        q.A = Lm; q.lda = s; q.sa = escr; q.alpha = -1.0;
+        q.B = Sg + s; q.ldb = n; q.sb = escr;
+        q.A2 = T; q.lda2 = s; q.sa2 = escr; q.alpha2 = 1.0;
+        q.B2 = Lm; q.ldb2 = s; q.sb2 = escr; q.opb2 = 1;
+        q.C = Sg + (int64_t)s * n + s; q.ldc = n; q.sc = escr; q.beta = 1.0;
         q.D = rmat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
         gemm_ok(q); add_gemm(q, g[1], maps[1], &lv.st[1], sa);
       }
@@ -324,13 +375,15 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     lv.nops = (int)ops.size();
     lv.asmops = ar.put(asmops);
     lv.row_op = ar.put(row_op);
-    lv.inv = ar.put(inv);
+    for (int c = 0; c < 4; ++c) {
+      lv.inv[c] = ar.put(inv[c]);
+      lv.ninv[c] = (int)inv[c].size();
+    }
     lv.trsm = ar.put(trs);
     for (int c = 0; c < 2; ++c) {
       lv.trsm_map[c] = ar.put(trs_map[c]);
       lv.ntrsm[c] = (int)trs_map[c].size();
     }
-    lv.nlu = (int)inv.size();
     lv.nstages = lesser ? 2 : 1;
     for (int k = 0; k < lv.nstages; ++k) {
       lv.st[k].ops = ar.put(g[k]);
@@ -339,7 +392,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         lv.st[k].nmap[c] = (int)maps[k][c].size();
       }
     }
-    scratch_elems = std::max(scratch_elems, off);
+    scratch_elems = escr;
     levels.push_back(lv);
   };
 
@@ -354,14 +407,14 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     lv.leaf = true;
     std::vector<findgb::AsmOp> asmops;
     std::vector<int> row_op;
-    std::vector<findgb::InvOp> inv;
+    std::vector<findgb::InvOp> inv[4];
     std::vector<findgb::GemmOp> g[2];
     std::vector<int> maps[2][6];
     std::vector<findgb::ExtractOp> ext;
     int64_t off = 0;
     for (const auto& op : p.leaf_ops) {
       const int64_t slot = leaf_slot_elems(op, lesser);
-      cplx* M = S0 + off * batch;
+      cplx* M = S0 + off;  // energy e at M + e * escr
       cplx* Sg = M + (int64_t)op.n * op.n;
       cplx* P = M + 2 * (int64_t)op.n * op.n;
       cplx* Q = P + (int64_t)op.c * op.n;
@@ -374,12 +427,12 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       a.u1 = umat(op.src); a.r1 = rmat(op.src); a.d1 = op.src < 0 ? 0 : p.mat_dim[op.src];
       a.u2 = nullptr; a.r2 = nullptr; a.d2 = 0;
       a.M = M;
-      a.estride = slot;
+      a.estride = escr;
       for (int r = 0; r < n; ++r) row_op.push_back((int)asmops.size());
       lv.nrows += n;
       asmops.push_back(a);
       if (bc) {
-        bc->block(M, lesser ? 2 * (int64_t)n + 2 * op.c : n, n, n, slot, batch, "leaf scratch");
+        bc->block(M, lesser ? 2 * (int64_t)n + 2 * op.c : n, n, n, escr, batch, "leaf scratch");
         if (a.u1) bc->block(a.u1, a.d1, a.d1, a.d1, (int64_t)a.d1 * a.d1, batch, "leaf U");
         if (a.r1) bc->block(a.r1, a.d1, a.d1, a.d1, (int64_t)a.d1 * a.d1, batch, "leaf R");
         for (int q = 0; q < n && bc->err.empty(); ++q) {
@@ -394,32 +447,37 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
             bc->err = "leaf bond index out of range";
         }
       }
-      inv.push_back(findgb::InvOp{M, slot, n, n, nullptr, 0});
+      {
+        const bool leaf_ff = ff_all && p.cl[op.cluster].depth > top_levels;
+        const int lc = (leaf_ff ? 1 : 0) + (n <= inv_smem ? 2 : 0);
+        inv[lc].push_back(findgb::InvOp{M, escr, n, n, nullptr, 0});
+        lv.inv_max[lc] = std::max(lv.inv_max[lc], n);
+        lv.fl_inv[lc] += 8.0 * (double)n * n * n;
+      }
       lv.max_s = std::max(lv.max_s, n);
-      lv.fl_inv += 8.0 * (double)n * n * n;
       lv.by_asm += 16.0 * ((lesser ? 2.0 : 1.0) * n * n + (lesser ? 2.0 : 1.0) * (double)a.d1 * a.d1);
       lv.by_ext += 16.0 * (lesser ? 2.0 : 1.0) * op.c + (lesser ? 24.0 * op.nbond : 0.0);
       if (lesser) {
         // P = G_K(C, :) Sigma_K
         findgb::GemmOp q = gemm0();
         q.m = op.c; q.n = n; q.k = n;
-        q.A = M + (int64_t)op.nb * n; q.lda = n; q.sa = slot;
-        q.B = Sg; q.ldb = n; q.sb = slot;
-        q.D = P; q.ldd = n; q.sd = slot;
+        q.A = M + (int64_t)op.nb * n; q.lda = n; q.sa = escr;
+        q.B = Sg; q.ldb = n; q.sb = escr;
+        q.D = P; q.ldd = n; q.sd = escr;
         const Arith la = (mixed && p.cl[op.cluster].depth > top_levels) ? kC64 : kFP64;
         gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], la);
         // Q = P G_K^H = G<_K(C, :)
         q = gemm0();
         q.m = op.c; q.n = n; q.k = n;
-        q.A = P; q.lda = n; q.sa = slot;
-        q.B = M; q.ldb = n; q.sb = slot; q.opb = 1;
-        q.D = Q; q.ldd = n; q.sd = slot;
+        q.A = P; q.lda = n; q.sa = escr;
+        q.B = M; q.ldb = n; q.sb = escr; q.opb = 1;
+        q.D = Q; q.ldd = n; q.sd = escr;
         gemm_ok(q); add_gemm(q, g[1], maps[1], &lv.st[1], la);
       }
       findgb::ExtractOp x;
       x.K = M;
       x.Q = lesser ? Q : nullptr;
-      x.estride = slot;
+      x.estride = escr;
       x.n = n; x.nb = op.nb; x.c = op.c;
       x.x0 = op.x0; x.y0 = op.y0; x.wx = op.wx;
       x.bond = op.bond; x.nbond = op.nbond;
@@ -428,7 +486,10 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     lv.nops = (int)p.leaf_ops.size();
     lv.asmops = ar.put(asmops);
     lv.row_op = ar.put(row_op);
-    lv.inv = ar.put(inv);
+    for (int c = 0; c < 4; ++c) {
+      lv.inv[c] = ar.put(inv[c]);
+      lv.ninv[c] = (int)inv[c].size();
+    }
     lv.ext = ar.put(ext);
     lv.nstages = lesser ? 2 : 0;
     for (int k = 0; k < lv.nstages; ++k) {
@@ -438,7 +499,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         lv.st[k].nmap[c] = (int)maps[k][c].size();
       }
     }
-    scratch_elems = std::max(scratch_elems, off);
+    scratch_elems = escr;
     levels.push_back(lv);
   }
 }
@@ -492,6 +553,9 @@ double workspace_bytes(find_handle* h, int batch, bool lesser, std::string* chec
     Bounds bc;
     bc.lo = fake;
     bc.hi = fake + L.meta;
+    bc.s_lo = fake + L.scratch;
+    bc.s_hi = fake + L.scratch + (size_t)se * batch * sizeof(cplx);
+    bc.s_stride = se * (int64_t)sizeof(cplx);
     build_tables(h, fake, L, batch, lesser, a2, lv, se, &bc);
     *check_err = bc.err;
   }
@@ -526,6 +590,9 @@ int ensure_workspace(find_handle* h, int batch, bool lesser) {
   Bounds bc;
   bc.lo = ws;
   bc.hi = ws + L.meta;
+  bc.s_lo = ws + L.scratch;
+  bc.s_hi = ws + L.scratch + (size_t)se * batch * sizeof(cplx);
+  bc.s_stride = se * (int64_t)sizeof(cplx);
   build_tables(h, ws, L, batch, lesser, real, h->levels, se, &bc);
   if (!bc.err.empty()) {
     release(h);
@@ -567,10 +634,10 @@ const T* at(const find_handle* h, size_t off) {
   return reinterpret_cast<const T*>(h->ws + h->lay.meta + off);
 }
 
-const int kClasses = 13;
+const int kClasses = 15;
 const char* kClassNames[kClasses] = {"lead",    "assemble", "invert",   "lu",       "trsm",
                                      "zgemm32", "zgemm64",  "extract",  "cgemm32",  "cgemm64",
-                                     "ffgemm32", "ffgemm64", "fftrsm"};
+                                     "ffgemm32", "ffgemm64", "fftrsm",  "fflu",     "ffinvert"};
 // profiler class of each GEMM launch class 2 * arith + big
 const int kGemmClass[6] = {5, 6, 8, 9, 10, 11};
 
@@ -601,28 +668,32 @@ void timed(find_handle* h, cudaStream_t st, int cls, double flops, double bytes,
 
 void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, bool lesser,
                int e_base, int nb, cudaStream_t st, cplx* oG, cplx* oGl, double* oJ,
-               int want_bonds) {
+               int want_bonds, int e_off = 0) {
   const Layout& L = h->lay;
   auto pos = reinterpret_cast<const findgb::Pos*>(h->ws + L.pos);
   int* status = reinterpret_cast<int*>(h->ws + L.status);
   timed(h, st, 1, 0.0, lv.by_asm * nb, [&] {
     findgb::launch_assemble(at<findgb::AsmOp>(h, lv.asmops), at<int>(h, lv.row_op), lv.nrows, pos,
-                            P, lesser ? 1 : 0, nb, st);
+                            P, lesser ? 1 : 0, nb, st, e_off);
   });
   if (lv.leaf) {
-    if (lv.max_s > 0)
-      timed(h, st, 2, lv.fl_inv * nb, 0.0, [&] {
-        findgb::launch_invert(at<findgb::InvOp>(h, lv.inv), lv.nops, lv.max_s, status, e_base, nb, st);
-      });
-  } else if (lv.nlu > 0) {
-    timed(h, st, 3, lv.fl_lu * nb, 0.0, [&] {
-      findgb::launch_lu(at<findgb::InvOp>(h, lv.inv), lv.nlu, status, e_base, nb, st);
-    });
+    for (int c = 0; c < 4; ++c)
+      if (lv.ninv[c] > 0)
+        timed(h, st, (c & 1) ? 14 : 2, lv.fl_inv[c] * nb, 0.0, [&] {
+          findgb::launch_invert(at<findgb::InvOp>(h, lv.inv[c]), lv.ninv[c], lv.inv_max[c], status,
+                                e_base, nb, st, e_off, c & 1, c >> 1);
+        });
+  } else {
+    for (int c = 0; c < 2; ++c)
+      if (lv.ninv[c] > 0)
+        timed(h, st, c ? 13 : 3, lv.fl_inv[c] * nb, 0.0, [&] {
+          findgb::launch_lu(at<findgb::InvOp>(h, lv.inv[c]), lv.ninv[c], status, e_base, nb, st, e_off, c);
+        });
     for (int c = 0; c < 2; ++c)
       if (lv.ntrsm[c] > 0)
         timed(h, st, c ? 12 : 4, lv.fl_trsm[c] * nb, 0.0, [&] {
           findgb::launch_trsm(at<findgb::TrsmOp>(h, lv.trsm), at<int>(h, lv.trsm_map[c]), lv.ntrsm[c],
-                              lv.rb, lv.max_s, nb, st, c);
+                              lv.rb, lv.max_s, nb, st, c, e_off);
         });
   }
   for (int k = 0; k < lv.nstages; ++k) {
@@ -631,7 +702,7 @@ void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, boo
     for (int c = 0; c < 6; ++c)
       if (s.nmap[c])
         timed(h, st, kGemmClass[c], s.fl[c] * nb, 0.0, [&] {
-          findgb::launch_gemm(ops, at<int>(h, s.map[c]), s.nmap[c], c & 1, nb, st, c >> 1);
+          findgb::launch_gemm(ops, at<int>(h, s.map[c]), s.nmap[c], c & 1, nb, st, c >> 1, e_off);
         });
   }
   if (lv.leaf)
@@ -639,8 +710,29 @@ void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, boo
       findgb::launch_extract(at<findgb::ExtractOp>(h, lv.ext), lv.nops,
                              reinterpret_cast<const findgb::LeafBond*>(h->ws + L.bonds), P,
                              lesser ? 1 : 0, want_bonds, oG, oGl, oJ,
-                             (int64_t)h->plan.nx * h->plan.ny, h->plan.n_bonds, nb, st);
+                             (int64_t)h->plan.nx * h->plan.ny, h->plan.n_bonds, nb, st, e_off);
     });
+}
+
+// Streams and events of the concurrent energy groups, created once per
+// handle: kMaxGroups streams, one join event per group and the fork event
+// at index kMaxGroups.
+constexpr int kMaxGroups = 4;
+
+int ensure_group_streams(find_handle* h) {
+  while ((int)h->gstreams.size() < kMaxGroups) {
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(h, e, "group stream");
+    h->gstreams.push_back(s);
+  }
+  while ((int)h->gevents.size() < kMaxGroups + 1) {
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(h, e, "group event");
+    h->gevents.push_back(ev);
+  }
+  return FIND_OK;
 }
 
 int solve(find_handle* h, const double* E, int nE, const double* sigL, const double* sigR,
@@ -727,7 +819,30 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
                        : nullptr;
     double* oJ = want_bonds ? (dJ ? J + (int64_t)e0 * p.n_bonds : reinterpret_cast<double*>(ws + L.oJ))
                             : nullptr;
-    for (const Level& lv : h->levels) run_level(h, lv, P, lesser, e0, nb, st, oG, oGl, oJ, want_bonds);
+    // independent energy groups on their own streams, so that one group's
+    // low-parallelism phases (LU of the few large top blocks) overlap other
+    // groups' work
+    const int gsz = h->desc.energy_group > 0 ? h->desc.energy_group : 8;
+    const int ng = std::min((nb + gsz - 1) / gsz, kMaxGroups);
+    if (ng <= 1) {
+      for (const Level& lv : h->levels) run_level(h, lv, P, lesser, e0, nb, st, oG, oGl, oJ, want_bonds);
+    } else {
+      int rc2 = ensure_group_streams(h);
+      if (rc2 != FIND_OK) return rc2;
+      cudaEvent_t fork = h->gevents[kMaxGroups];
+      cudaEventRecord(fork, st);
+      const int per = (nb + ng - 1) / ng;
+      for (int g = 0; g < ng; ++g) {
+        const int lo = g * per, cnt = std::min(per, nb - lo);
+        if (cnt <= 0) continue;
+        cudaStream_t gs = h->gstreams[g];
+        cudaStreamWaitEvent(gs, fork, 0);
+        for (const Level& lv : h->levels)
+          run_level(h, lv, P, lesser, e0, cnt, gs, oG, oGl, oJ, want_bonds, lo);
+        cudaEventRecord(h->gevents[g], gs);
+        cudaStreamWaitEvent(st, h->gevents[g], 0);
+      }
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
     if (!dG) {
@@ -793,11 +908,13 @@ void run_level_static(find_handle* h, const StaticView& sv, const Level& lv,
   findgb::launch_assemble(reinterpret_cast<const findgb::AsmOp*>(meta(lv.asmops)),
                           reinterpret_cast<const int*>(meta(lv.row_op)), lv.nrows, pos, P, 0, nb, st);
   if (lv.leaf) {
-    if (lv.max_s > 0)
-      findgb::launch_invert(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv)), lv.nops, lv.max_s,
-                            status, e_base, nb, st);
-  } else if (lv.nlu > 0) {
-    findgb::launch_lu(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv)), lv.nlu, status, e_base, nb, st);
+    for (int c = 0; c < 4; ++c)
+      findgb::launch_invert(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv[c])), lv.ninv[c],
+                            lv.inv_max[c], status, e_base, nb, st, 0, c & 1, c >> 1);
+  } else {
+    for (int c = 0; c < 2; ++c)
+      findgb::launch_lu(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv[c])), lv.ninv[c], status,
+                        e_base, nb, st, 0, c);
     for (int c = 0; c < 2; ++c)
       findgb::launch_trsm(reinterpret_cast<const findgb::TrsmOp*>(meta(lv.trsm)),
                           reinterpret_cast<const int*>(meta(lv.trsm_map[c])), lv.ntrsm[c], lv.rb,
@@ -854,6 +971,9 @@ int solve_static(find_handle* h, const double* E, int nE, const double* sigL, co
     Bounds bc;
     bc.lo = base;
     bc.hi = base + L.meta;
+    bc.s_lo = base + L.scratch;
+    bc.s_hi = base + L.scratch + (size_t)se * batch * sizeof(cplx);
+    bc.s_stride = se * (int64_t)sizeof(cplx);
     build_tables(h, base, L, batch, false, real, lv, se, &bc);
     if (!bc.err.empty() || L.total > kStaticScratchBytes)
       return fail(h, FIND_EINVAL, "internal table check failed for the fixed scratch: " + bc.err);
@@ -949,8 +1069,8 @@ extern "C" {
 int find_create(const find_desc* d, find_handle** out) {
   if (!d || !out) return fail(nullptr, FIND_EINVAL, "null descriptor or output");
   *out = nullptr;
-  if (d->precision != FIND_FP64 && d->precision != FIND_MIXED)
-    return fail(nullptr, FIND_EINVAL, "precision must be FIND_FP64 or FIND_MIXED");
+  if (d->precision != FIND_FP64 && d->precision != FIND_MIXED && d->precision != FIND_MIXED_FF)
+    return fail(nullptr, FIND_EINVAL, "precision must be FIND_FP64, FIND_MIXED or FIND_MIXED_FF");
   if (d->stencil != 5 && d->stencil != 9) return fail(nullptr, FIND_EINVAL, "stencil must be 5 or 9");
   if (d->max_batch < 0) return fail(nullptr, FIND_EINVAL, "max_batch < 0");
   find_handle* h = new (std::nothrow) find_handle();
@@ -1093,6 +1213,8 @@ int find_destroy(find_handle* h) {
       cudaEventDestroy(p.b);
     }
     for (auto e : h->ev_free) cudaEventDestroy(e);
+    for (auto e : h->gevents) cudaEventDestroy(e);
+    for (auto q : h->gstreams) cudaStreamDestroy(q);
   }
   delete h;
   return FIND_OK;

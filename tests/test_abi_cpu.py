@@ -118,7 +118,7 @@ def test_workspace_grows_linearly_with_batch(F):
 def test_descriptor_tables_stay_in_bounds(F, nx, ny, stencil, leaf):
     # every operand of every kernel launch lies inside the workspace, for
     # several batch sizes, in both the diag and the lesser configuration
-    for precision in ("fp64", "mixed"):
+    for precision in ("fp64", "mixed", "mixed_ff"):
         f = F.Find(nx, ny, stencil, 1.0, 0.2, leaf=leaf, precision=precision)
         for batch in (1, 3, 8):
             for lesser in (False, True):

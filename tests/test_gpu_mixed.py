@@ -1,6 +1,7 @@
-"""Mixed path (FIND_MIXED): below the top FP64 levels the Sigma update and
+"""Mixed paths.  FIND_MIXED: below the top FP64 levels the Sigma update and
 the leaf G< products run in complex64, the Schur update U and the solves for
 L in float-float (about 48 significant bits); LU and leaf inversion in FP64.
+FIND_MIXED_FF: the LU and the leaf inversion in float-float as well.
 Bar: 1e-5 normwise per energy against the FP64 oracle for diag G and diag G<
 (diag G, fed only by float-float and FP64 steps, is held to 1e-9)."""
 
@@ -39,9 +40,10 @@ def solve(F, mesh, Es, precision, leaf=8, top=2, max_batch=0):
     return out
 
 
-def test_c2_mixed_all_energies_within_1e5(F):
+@pytest.mark.parametrize("precision", ["mixed", "mixed_ff"])
+def test_c2_mixed_all_energies_within_1e5(F, precision):
     mesh, Es = W.c2(), W.c2_energies()
-    G, Gl, J = solve(F, mesh, Es, "mixed", leaf=5)
+    G, Gl, J = solve(F, mesh, Es, precision, leaf=5)
     P = problem.MeshProblem.from_mesh(mesh)
     worst = 0.0
     for k in range(0, 64, 4):
@@ -55,11 +57,12 @@ def test_c2_mixed_all_energies_within_1e5(F):
 # With the default two FP64 top levels the bar is 1e-5; with none the Sigma
 # update of the largest blocks also runs in complex64 and one energy of this
 # mesh reached 1.002e-5, so that setting is held to 3e-5.
-@pytest.mark.parametrize("top,tol", [(2, TOL_MIXED), (0, 3e-5)])
-def test_mixed_9pt_mesh_against_oracle_find(F, top, tol):
+@pytest.mark.parametrize("precision,top,tol", [("mixed", 2, TOL_MIXED), ("mixed", 0, 3e-5),
+                                               ("mixed_ff", 2, TOL_MIXED)])
+def test_mixed_9pt_mesh_against_oracle_find(F, precision, top, tol):
     mesh = W.Mesh(64, 128, 9, 1.0, 0.2, -1.0, 1.0, 1109)
     Es = W.c5_energies()[[0, 100, 300, 400, 511]]
-    G, Gl, J = solve(F, mesh, Es, "mixed", top=top)
+    G, Gl, J = solve(F, mesh, Es, precision, top=top)
     P = problem.MeshProblem.from_mesh(mesh)
     for k, E in enumerate(Es):
         rG, rGl, _, _ = ofind.find_outputs(P, E, leaf=8, bonds=False)
@@ -67,11 +70,12 @@ def test_mixed_9pt_mesh_against_oracle_find(F, top, tol):
         assert rel(Gl[k], rGl) <= tol, (E, rel(Gl[k], rGl))
 
 
-def test_mixed_alone_and_in_batch_are_bitwise_equal(F):
+@pytest.mark.parametrize("precision", ["mixed", "mixed_ff"])
+def test_mixed_alone_and_in_batch_are_bitwise_equal(F, precision):
     mesh = W.Mesh(24, 40, 9, 1.0, 0.2, -1.0, 1.0, 81)
     Es = W.energy_grid(0.2, 7.8, 6)
-    both = solve(F, mesh, Es, "mixed", leaf=5, max_batch=6)
+    both = solve(F, mesh, Es, precision, leaf=5, max_batch=6)
     for k in (1, 5):
-        alone = solve(F, mesh, Es[k:k + 1], "mixed", leaf=5, max_batch=1)
+        alone = solve(F, mesh, Es[k:k + 1], precision, leaf=5, max_batch=1)
         for a, b in zip(alone, both):
             assert np.array_equal(a[0], b[k])
