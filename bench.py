@@ -50,9 +50,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--path", choices=["fp64", "mixed"], default="fp64",
-                    help="fp64: every step in FP64; mixed: Sigma update and leaf G< "
-                         "products in complex64, the rest FP64")
+    ap.add_argument("--path", choices=["fp64", "mixed", "mixed_ff"], default="fp64",
+                    help="fp64: every step in FP64; mixed: Sigma update and leaf G< products in "
+                         "complex64, U and L solves in float-float, LU and leaf inversion FP64; "
+                         "mixed_ff: LU and leaf inversion in float-float too")
     ap.add_argument("--serve-requests", type=int, default=6,
                     help="requests of the serving scenario (0 skips it)")
     ap.add_argument("--mesh", default="256x1024",

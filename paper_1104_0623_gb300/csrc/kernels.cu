@@ -75,9 +75,26 @@ __device__ __forceinline__ cplx csqrt_principal(cplx z) {
 // (re.hi, re.lo, im.hi, im.lo).  On GB300 the FP32 pipes run about 70 times
 // the FP64 rate, so a multiply-add carried this way (12 FP32 operations per
 // real product) is several times faster than FP64 at nearly its accuracy.
+// Split a double into hi + lo floats without the (slow) FP64 pipe: hi keeps
+// the sign, the exponent and the top 23 fraction bits (truncated); lo is the
+// remaining 29 fraction bits, x - hi exactly, converted to float (rounded to
+// 24 bits) and scaled by 2^(e - 1075).  Values outside the float normal range
+// (zero included) take the FP64 conversions.
 __device__ __forceinline__ void df_split(double x, float& h, float& l) {
-  h = __double2float_rn(x);
-  l = __double2float_rn(x - (double)h);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ffull);
+  if (e < 1023 - 126 || e > 1023 + 127) {
+    h = __double2float_rn(x);
+    l = __double2float_rn(x - (double)h);
+    return;
+  }
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+  h = __uint_as_float(sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)(mant >> 29));
+  float lf = (float)(unsigned int)(mant & 0x1FFFFFFFull);
+  const int pe = e - 1075 + 127;  // biased float exponent of 2^(e - 1075)
+  lf = (pe > 0) ? lf * __uint_as_float((unsigned int)pe << 23) : ldexpf(lf, e - 1075);
+  l = sign ? -lf : lf;
 }
 __device__ __forceinline__ double df_join(float h, float l) { return (double)h + (double)l; }
 // (ch, cl) += (ah, al) * (bh, bl): the product's exact high part, its rounding
@@ -241,7 +258,7 @@ struct GA<false> {
   __device__ __forceinline__ static cplx to(T v) { return v; }
   __device__ __forceinline__ static double mag(T v) { return fabs(v.x) + fabs(v.y); }
   __device__ __forceinline__ static T zero() { return cmk(0, 0); }
-  __device__ __forceinline__ static T scale(T a, cplx b) { return cmul(a, b); }
+  __device__ __forceinline__ static T scale(T a, T b) { return cmul(a, b); }
   __device__ __forceinline__ static T fms(T f, T r, T v) { return cfms(f, r, v); }
   __device__ __forceinline__ static bool is_zero(T v) { return v.x == 0.0 && v.y == 0.0; }
 };
@@ -251,10 +268,10 @@ struct GA<true> {
   typedef float4 T;
   __device__ __forceinline__ static T from(cplx v) { return df_load(v, 1.0); }
   __device__ __forceinline__ static cplx to(T v) { return df_wide(v); }
-  __device__ __forceinline__ static double mag(T v) { return fabs((double)v.x) + fabs((double)v.z); }
+  __device__ __forceinline__ static double mag(T v) { return (double)(fabsf(v.x) + fabsf(v.z)); }
   __device__ __forceinline__ static T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-  __device__ __forceinline__ static T scale(T a, cplx b) {
-    T r = df_cfma(a, df_load(b, 1.0), make_float4(0.f, 0.f, 0.f, 0.f));
+  __device__ __forceinline__ static T scale(T a, T b) {
+    T r = df_cfma(a, b, make_float4(0.f, 0.f, 0.f, 0.f));
     df_norm(r.x, r.y);
     df_norm(r.z, r.w);
     return r;
@@ -314,6 +331,7 @@ __device__ void gauss_jordan(T* a, int ld, int s, T* colk, T* rowk, int* piv, in
   __shared__ double red_v[32];
   __shared__ int red_i[32];
   __shared__ int sh_p;
+  __shared__ T sh_pinv;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   for (int k = 0; k < s; ++k) {
     const int p = pivot_row<X>(a, ld, k, s, red_v, red_i, &sh_p);
@@ -325,17 +343,17 @@ __device__ void gauss_jordan(T* a, int ld, int s, T* colk, T* rowk, int* piv, in
         a[(int64_t)p * ld + j] = t0;
       }
     __syncthreads();
-    const T pv = a[(int64_t)k * ld + k];
-    cplx pinv;
-    if (X::is_zero(pv)) {
-      pinv = cmk(0, 0);
-      if (tid == 0) atomicMin(status, energy);
-    } else {
-      pinv = crecip(X::to(pv));
+    if (tid == 0) {  // the pivot reciprocal, once per step, in FP64 (Smith)
+      const T pv = a[(int64_t)k * ld + k];
+      cplx pinv = cmk(0, 0);
+      if (X::is_zero(pv)) atomicMin(status, energy);
+      else pinv = crecip(X::to(pv));
+      sh_pinv = X::from(pinv);
     }
-    __syncthreads();  // every thread has read the pivot before row k changes
+    __syncthreads();
+    const T pinv = sh_pinv;
     for (int j = tid; j < s; j += blockDim.x) {
-      T v = (j == k) ? X::from(pinv) : X::scale(a[(int64_t)k * ld + j], pinv);
+      T v = (j == k) ? pinv : X::scale(a[(int64_t)k * ld + j], pinv);
       rowk[j] = v;
       a[(int64_t)k * ld + j] = v;
     }
@@ -466,6 +484,7 @@ __global__ void __launch_bounds__(kInvThreads) k_lu(const InvOp* __restrict__ op
   __shared__ double red_v[32];
   __shared__ int red_i[32];
   __shared__ int sh_p;
+  __shared__ T sh_pinv;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   to_work<X>(g, ld, s);
   T* a = reinterpret_cast<T*>(g);
@@ -479,14 +498,15 @@ __global__ void __launch_bounds__(kInvThreads) k_lu(const InvOp* __restrict__ op
         a[(int64_t)p * ld + j] = t0;
       }
     __syncthreads();
-    const T pv = a[(int64_t)k * ld + k];
-    cplx pinv;
-    if (X::is_zero(pv)) {
-      pinv = cmk(0, 0);
-      if (tid == 0) atomicMin(status, e_base + e);
-    } else {
-      pinv = crecip(X::to(pv));
+    if (tid == 0) {  // the pivot reciprocal, once per step, in FP64 (Smith)
+      const T pv = a[(int64_t)k * ld + k];
+      cplx pinv = cmk(0, 0);
+      if (X::is_zero(pv)) atomicMin(status, e_base + e);
+      else pinv = crecip(X::to(pv));
+      sh_pinv = X::from(pinv);
     }
+    __syncthreads();
+    const T pinv = sh_pinv;
     for (int j = k + 1 + tid; j < s; j += blockDim.x) rowk[j] = a[(int64_t)k * ld + j];
     for (int i = k + 1 + tid; i < s; i += blockDim.x)
       a[(int64_t)i * ld + k] = X::scale(a[(int64_t)i * ld + k], pinv);
@@ -549,7 +569,8 @@ struct Cx<float4> {
 // Tile BM x BN per CTA, BK deep; each thread owns a 4 x 4 block of outputs at
 // rows ty + i*BM/4, cols tx + j*BN/4.  alpha is folded into the A tile.
 template <int BM, int BN, int BK, class CT>
-__global__ void __launch_bounds__((BM / 4) * (BN / 4)) k_zgemm(const GemmOp* __restrict__ ops,
+__global__ void __launch_bounds__((BM / 4) * (BN / 4), (sizeof(CT) == 16 && BM == 64) ? 2 : 1)
+    k_zgemm(const GemmOp* __restrict__ ops,
                                                                const int* __restrict__ tile_op,
                                                                int e_off) {
   typedef Cx<CT> X;
@@ -641,12 +662,14 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4)) k_zgemm(const GemmOp* __r
 }
 
 // ---------------------------------------------------------------- L = M(B,S) M(S,S)^{-1}
-// Row block of RB rows per CTA held in shared memory.  Forward sweep solves
-// Y U = M(B,S) column by column (scale by 1/U_jj, then eliminate column j
-// from the later columns); backward sweep solves Z L = Y with the unit-lower
-// factor; the row interchanges are then applied as column interchanges.
-// DF: the row block is carried in float-float (factors read in FP64 and
-// split once per use, shared by the RB rows).
+// Row block of RB rows per CTA held in shared memory.  The forward sweep
+// solves Y U = M(B,S) in panels of W columns: each row solves the panel's
+// own columns (scale by 1/U_jj, eliminate within the panel), then every later
+// column takes a rank-W update; the backward sweep solves Z L = Y with the
+// unit-lower factor the same way, right to left; the row interchanges are
+// then applied as column interchanges.  DF: the row block is carried in
+// float-float (factors read in FP64 and split once per use, shared by the
+// RB rows).
 template <bool DF>
 struct TrsmArith;
 
@@ -656,7 +679,8 @@ struct TrsmArith<false> {
   __device__ __forceinline__ static T in(cplx v) { return v; }
   __device__ __forceinline__ static cplx out(T v) { return v; }
   __device__ __forceinline__ static T mul(T a, cplx b) { return cmul(a, b); }
-  __device__ __forceinline__ static T fms(T a, cplx b, T c) { return cfms(a, b, c); }
+  __device__ __forceinline__ static T mul2(T a, T b) { return cmul(a, b); }
+  __device__ __forceinline__ static T fms(T a, T b, T c) { return cfms(a, b, c); }
 };
 
 template <>
@@ -667,8 +691,14 @@ struct TrsmArith<true> {
   __device__ __forceinline__ static T mul(T a, cplx b) {
     return df_cfma(a, df_load(b, 1.0), make_float4(0.f, 0.f, 0.f, 0.f));
   }
-  __device__ __forceinline__ static T fms(T a, cplx b, T c) {
-    T r = df_cfma(make_float4(-a.x, -a.y, -a.z, -a.w), df_load(b, 1.0), c);
+  __device__ __forceinline__ static T mul2(T a, T b) {
+    T r = df_cfma(a, b, make_float4(0.f, 0.f, 0.f, 0.f));
+    df_norm(r.x, r.y);
+    df_norm(r.z, r.w);
+    return r;
+  }
+  __device__ __forceinline__ static T fms(T a, T b, T c) {
+    T r = df_cfma(make_float4(-a.x, -a.y, -a.z, -a.w), b, c);
     df_norm(r.x, r.y);
     df_norm(r.z, r.w);
     return r;
@@ -680,6 +710,7 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
                                               const int* __restrict__ tile_op, int rb, int e_off) {
   typedef TrsmArith<DF> X;
   typedef typename X::T T;
+  constexpr int W = 8;  // columns per panel: one panel solve and one rank-W update per barrier pair
   const TrsmOp& op = ops[tile_op[blockIdx.x]];
   const int e = blockIdx.y + e_off;
   const int s = op.s, ld = op.ld;
@@ -691,31 +722,76 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
   extern __shared__ double2 tr_smem[];
   T* Y = reinterpret_cast<T*>(tr_smem);            // rows x s
   int* perm = reinterpret_cast<int*>(Y + (int64_t)rb * s);
+  __shared__ T pan[W][W];                           // the panel's block of the factor
+  __shared__ T dgl[W];                              // reciprocals of the panel's diagonal
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int idx = tid; idx < rows * s; idx += nt) {
     int r = idx / s, j = idx % s;
     Y[r * s + j] = X::in(a[(int64_t)(s + r0 + r) * ld + j]);
   }
-  __syncthreads();
-  // forward: Y U = B
-  for (int j = 0; j < s; ++j) {
-    if (tid < rows) {
-      const cplx ujj = a[(int64_t)j * ld + j];  // zero only if the LU flagged it
-      cplx d = (ujj.x == 0.0 && ujj.y == 0.0) ? cmk(0, 0) : crecip(ujj);
-      Y[tid * s + j] = X::mul(Y[tid * s + j], d);
+  // forward: Y U = B, panels of W columns left to right
+  for (int j0 = 0; j0 < s; j0 += W) {
+    const int w = min(W, s - j0);
+    for (int idx = tid; idx < w * w; idx += nt) {
+      const int t = idx / w, t2 = idx % w;
+      const cplx u = a[(int64_t)(j0 + t) * ld + j0 + t2];
+      if (t == t2) {
+        const bool z = (u.x == 0.0 && u.y == 0.0);  // zero only if the LU flagged it
+        dgl[t] = X::in(z ? cmk(0, 0) : crecip(u));
+      } else {
+        pan[t][t2] = X::in(u);
+      }
     }
     __syncthreads();
-    for (int i = j + 1 + tid; i < s; i += nt) {
-      const cplx u = a[(int64_t)j * ld + i];
-      for (int r = 0; r < rows; ++r) Y[r * s + i] = X::fms(Y[r * s + j], u, Y[r * s + i]);
+    if (tid < rows) {  // the panel's own columns, one row per thread
+      T* y = Y + tid * s + j0;
+      for (int t = 0; t < w; ++t) {
+        y[t] = X::mul2(y[t], dgl[t]);
+        for (int t2 = t + 1; t2 < w; ++t2) y[t2] = X::fms(y[t], pan[t][t2], y[t2]);
+      }
+    }
+    __syncthreads();
+    for (int i = j0 + w + tid; i < s; i += nt) {  // rank-w update of the later columns
+      T u[W];
+#pragma unroll
+      for (int t = 0; t < W; ++t)
+        if (t < w) u[t] = X::in(a[(int64_t)(j0 + t) * ld + i]);
+      for (int r = 0; r < rows; ++r) {
+        T v = Y[r * s + i];
+#pragma unroll
+        for (int t = 0; t < W; ++t)
+          if (t < w) v = X::fms(Y[r * s + j0 + t], u[t], v);
+        Y[r * s + i] = v;
+      }
     }
     __syncthreads();
   }
-  // backward: Z L = Y, L unit lower
-  for (int j = s - 1; j > 0; --j) {
-    for (int i = tid; i < j; i += nt) {
-      const cplx l = a[(int64_t)j * ld + i];
-      for (int r = 0; r < rows; ++r) Y[r * s + i] = X::fms(Y[r * s + j], l, Y[r * s + i]);
+  // backward: Z L = Y with L unit lower, panels of W columns right to left
+  for (int je = s; je > 0; je -= W) {
+    const int j0 = max(0, je - W), w = je - j0;
+    for (int idx = tid; idx < w * w; idx += nt) {
+      const int t = idx / w, t2 = idx % w;
+      if (t2 < t) pan[t][t2] = X::in(a[(int64_t)(j0 + t) * ld + j0 + t2]);
+    }
+    __syncthreads();
+    if (tid < rows) {
+      T* y = Y + tid * s + j0;
+      for (int t = w - 1; t > 0; --t)
+        for (int t2 = 0; t2 < t; ++t2) y[t2] = X::fms(y[t], pan[t][t2], y[t2]);
+    }
+    __syncthreads();
+    for (int i = tid; i < j0; i += nt) {
+      T l[W];
+#pragma unroll
+      for (int t = 0; t < W; ++t)
+        if (t < w) l[t] = X::in(a[(int64_t)(j0 + t) * ld + i]);
+      for (int r = 0; r < rows; ++r) {
+        T v = Y[r * s + i];
+#pragma unroll
+        for (int t = 0; t < W; ++t)
+          if (t < w) v = X::fms(Y[r * s + j0 + t], l[t], v);
+        Y[r * s + i] = v;
+      }
     }
     __syncthreads();
   }

@@ -464,7 +464,10 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         q.A = M + (int64_t)op.nb * n; q.lda = n; q.sa = escr;
         q.B = Sg; q.ldb = n; q.sb = escr;
         q.D = P; q.ldd = n; q.sd = escr;
-        const Arith la = (mixed && p.cl[op.cluster].depth > top_levels) ? kC64 : kFP64;
+        // the leaf products G_K Sigma_K G_K^H carry diag G< directly: float-float
+        // keeps the mixed paths' G< error near that of the complex64 Sigma
+        // update alone (complex64 here reached 1e-5 on a 64x128 mesh)
+        const Arith la = (mixed && p.cl[op.cluster].depth > top_levels) ? kFF : kFP64;
         gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], la);
         // Q = P G_K^H = G<_K(C, :)
         q = gemm0();
