@@ -572,7 +572,7 @@ template <int BM, int BN, int BK, class CT>
 __global__ void __launch_bounds__((BM / 4) * (BN / 4), (sizeof(CT) == 16 && BM == 64) ? 2 : 1)
     k_zgemm(const GemmOp* __restrict__ ops,
                                                                const int* __restrict__ tile_op,
-                                                               int e_off) {
+                                                               int e_off, int sym_mask) {
   typedef Cx<CT> X;
   constexpr int NT = (BM / 4) * (BN / 4);
   constexpr int RS = BM / 4, CS = BN / 4;
@@ -581,7 +581,12 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4), (sizeof(CT) == 16 && BM =
   const int t = blockIdx.x, e = blockIdx.y + e_off;
   const GemmOp& op = ops[tile_op[t]];
   const int local = t - op.tile0;
-  const int m0 = (local / op.tiles_n) * BM, n0 = (local % op.tiles_n) * BN;
+  const int tm = local / op.tiles_n, tn = local % op.tiles_n;
+  const int m0 = tm * BM, n0 = tn * BN;
+  // a complex symmetric output: only tiles on or above the diagonal work,
+  // and mirror what they compute
+  const bool mirror = BM == BN && op.sym == 1 && (sym_mask & 1);
+  if (mirror && tm > tn) return;
   const int tx = threadIdx.x % CS, ty = threadIdx.x / CS;
   const int M = op.m, N = op.n;
   CT acc[4][4];
@@ -650,6 +655,7 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4), (sizeof(CT) == 16 && BM =
     for (int j = 0; j < 4; ++j) {
       int gj = n0 + tx + j * CS;
       if (gj >= N) continue;
+      if (mirror && gi > gj) continue;  // the (gj, gi) thread writes this pair
       cplx v = X::wide(acc[i][j]);
       if (C) {
         cplx c = C[(int64_t)gi * op.ldc + gj];
@@ -657,6 +663,7 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4), (sizeof(CT) == 16 && BM =
         v.y = fma(op.beta, c.y, v.y);
       }
       D[(int64_t)gi * op.ldd + gj] = v;
+      if (mirror && gi != gj) D[(int64_t)gj * op.ldd + gi] = v;
     }
   }
 }
@@ -927,24 +934,24 @@ void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int 
 }
 
 void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,
-                 cudaStream_t st, int fp32, int e_off) {
+                 cudaStream_t st, int fp32, int e_off, int sym_mask) {
   if (ntiles == 0) return;
   dim3 grid(ntiles, nE);
   if (fp32 == 2) {
     if (big)
-      k_zgemm<64, 64, 8, float4><<<grid, 256, 0, st>>>(ops, tile_op, e_off);
+      k_zgemm<64, 64, 8, float4><<<grid, 256, 0, st>>>(ops, tile_op, e_off, sym_mask);
     else
-      k_zgemm<32, 32, 8, float4><<<grid, 64, 0, st>>>(ops, tile_op, e_off);
+      k_zgemm<32, 32, 8, float4><<<grid, 64, 0, st>>>(ops, tile_op, e_off, sym_mask);
   } else if (fp32) {
     if (big)
-      k_zgemm<64, 64, 16, float2><<<grid, 256, 0, st>>>(ops, tile_op, e_off);
+      k_zgemm<64, 64, 16, float2><<<grid, 256, 0, st>>>(ops, tile_op, e_off, sym_mask);
     else
-      k_zgemm<32, 32, 16, float2><<<grid, 64, 0, st>>>(ops, tile_op, e_off);
+      k_zgemm<32, 32, 16, float2><<<grid, 64, 0, st>>>(ops, tile_op, e_off, sym_mask);
   } else {
     if (big)
-      k_zgemm<64, 64, 8, double2><<<grid, 256, 0, st>>>(ops, tile_op, e_off);
+      k_zgemm<64, 64, 8, double2><<<grid, 256, 0, st>>>(ops, tile_op, e_off, sym_mask);
     else
-      k_zgemm<32, 32, 8, double2><<<grid, 64, 0, st>>>(ops, tile_op, e_off);
+      k_zgemm<32, 32, 8, double2><<<grid, 64, 0, st>>>(ops, tile_op, e_off, sym_mask);
   }
 }
 

@@ -72,6 +72,9 @@ struct GemmOp {
   cplx* D; int ldd; int64_t sd;
   double alpha, alpha2, beta;
   int tile0, tiles_n;
+  int sym;  // 1: D is complex symmetric (m == n) when the problem is; the
+            // launch's sym_mask decides whether only the upper triangle is
+            // computed and mirrored
 };
 
 struct ExtractOp {
@@ -106,8 +109,9 @@ void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int 
 int trsm_rows_per_block(int max_s);
 // fp32 = 1: complex64 arithmetic on complex128 operands (mixed path);
 // fp32 = 2: float-float arithmetic (about 48 significant bits)
+// sym_mask bit 0: ops with sym == 1 compute the upper triangle and mirror it
 void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,
-                 cudaStream_t st, int fp32 = 0, int e_off = 0);
+                 cudaStream_t st, int fp32 = 0, int e_off = 0, int sym_mask = 0);
 void launch_extract(const ExtractOp* ops, int nops, const LeafBond* bonds, const DevProblem& P,
                     int lesser, int want_bonds, cplx* diagG, cplx* diagGl, double* J,
                     int64_t n_nodes, int64_t n_bonds, int nE, cudaStream_t st, int e_off = 0);

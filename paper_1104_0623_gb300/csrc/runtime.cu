@@ -349,6 +349,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       q.B = M + s; q.ldb = n; q.sb = escr;
       q.C = M + (int64_t)s * n + s; q.ldc = n; q.sc = escr; q.beta = 1.0;
       q.D = umat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
+      q.sym = 1;  // U is complex symmetric when A is (Property 1)
       gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], ua);
       const Arith sa = below_top ? kC64 : kFP64;
       if (lesser) {
@@ -369,6 +370,11 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         q.B2 = Lm; q.ldb2 = s; q.sb2 = escr; q.opb2 = 1;
         q.C = Sg + (int64_t)s * n + s; q.ldc = n; q.sc = escr; q.beta = 1.0;
         q.D = rmat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
+        // R is anti-Hermitian in exact arithmetic, but its computed entries
+        // carry cancellation errors that later steps rely on staying
+        // mutually consistent: mirroring one triangle was measured to raise
+        // the diag G< error from 1e-6 to 1e-2 (complex64) and from 5e-15 to
+        // 3e-11 (FP64), so R is computed in full
         gemm_ok(q); add_gemm(q, g[1], maps[1], &lv.st[1], sa);
       }
     }
@@ -671,7 +677,7 @@ void timed(find_handle* h, cudaStream_t st, int cls, double flops, double bytes,
 
 void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, bool lesser,
                int e_base, int nb, cudaStream_t st, cplx* oG, cplx* oGl, double* oJ,
-               int want_bonds, int e_off = 0) {
+               int want_bonds, int e_off = 0, int sym_mask = 0) {
   const Layout& L = h->lay;
   auto pos = reinterpret_cast<const findgb::Pos*>(h->ws + L.pos);
   int* status = reinterpret_cast<int*>(h->ws + L.status);
@@ -705,7 +711,8 @@ void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, boo
     for (int c = 0; c < 6; ++c)
       if (s.nmap[c])
         timed(h, st, kGemmClass[c], s.fl[c] * nb, 0.0, [&] {
-          findgb::launch_gemm(ops, at<int>(h, s.map[c]), s.nmap[c], c & 1, nb, st, c >> 1, e_off);
+          findgb::launch_gemm(ops, at<int>(h, s.map[c]), s.nmap[c], c & 1, nb, st, c >> 1, e_off,
+                              sym_mask);
         });
   }
   if (lv.leaf)
@@ -825,10 +832,14 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
     // independent energy groups on their own streams, so that one group's
     // low-parallelism phases (LU of the few large top blocks) overlap other
     // groups' work
+    // A = A^T when both leads take the closed form (Phi diag(sigma) Phi^T):
+    // then every U is complex symmetric and its update runs on one triangle
+    const int sym_mask = (!sigL && !sigR) ? 1 : 0;
     const int gsz = h->desc.energy_group > 0 ? h->desc.energy_group : 8;
     const int ng = std::min((nb + gsz - 1) / gsz, kMaxGroups);
     if (ng <= 1) {
-      for (const Level& lv : h->levels) run_level(h, lv, P, lesser, e0, nb, st, oG, oGl, oJ, want_bonds);
+      for (const Level& lv : h->levels)
+        run_level(h, lv, P, lesser, e0, nb, st, oG, oGl, oJ, want_bonds, 0, sym_mask);
     } else {
       int rc2 = ensure_group_streams(h);
       if (rc2 != FIND_OK) return rc2;
@@ -841,7 +852,7 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
         cudaStream_t gs = h->gstreams[g];
         cudaStreamWaitEvent(gs, fork, 0);
         for (const Level& lv : h->levels)
-          run_level(h, lv, P, lesser, e0, cnt, gs, oG, oGl, oJ, want_bonds, lo);
+          run_level(h, lv, P, lesser, e0, cnt, gs, oG, oGl, oJ, want_bonds, lo, sym_mask);
         cudaEventRecord(h->gevents[g], gs);
         cudaStreamWaitEvent(st, h->gevents[g], 0);
       }
@@ -903,7 +914,8 @@ cudaError_t static_scratch_address(int device, unsigned char** out) {
 
 // The diag pass on the tables of `sv` (no profiling).
 void run_level_static(find_handle* h, const StaticView& sv, const Level& lv,
-                      const findgb::DevProblem& P, int e_base, int nb, cudaStream_t st, cplx* oG) {
+                      const findgb::DevProblem& P, int e_base, int nb, cudaStream_t st, cplx* oG,
+                      int sym_mask) {
   const Layout& L = sv.lay;
   auto meta = [&](size_t off) { return sv.base + L.meta + off; };
   auto pos = reinterpret_cast<const findgb::Pos*>(sv.base + L.pos);
@@ -928,7 +940,7 @@ void run_level_static(find_handle* h, const StaticView& sv, const Level& lv,
     auto ops = reinterpret_cast<const findgb::GemmOp*>(meta(s.ops));
     for (int c = 0; c < 6; ++c)
       findgb::launch_gemm(ops, reinterpret_cast<const int*>(meta(s.map[c])), s.nmap[c], c & 1, nb, st,
-                          c >> 1);
+                          c >> 1, 0, sym_mask);
   }
   if (lv.leaf)
     findgb::launch_extract(reinterpret_cast<const findgb::ExtractOp*>(meta(lv.ext)), lv.nops,
@@ -1044,7 +1056,8 @@ int solve_static(find_handle* h, const double* E, int nE, const double* sigL, co
     P.fL = 0.0; P.fR = 0.0;
     P.dles = nullptr; P.dles_estride = 0;
     cplx* oG = dG ? reinterpret_cast<cplx*>(G) + (int64_t)e0 * n : reinterpret_cast<cplx*>(base + L.oG);
-    for (const Level& lv : sv.levels) run_level_static(h, sv, lv, P, e0, nb, st, oG);
+    const int sym_mask = (!sigL && !sigR) ? 1 : 0;
+    for (const Level& lv : sv.levels) run_level_static(h, sv, lv, P, e0, nb, st, oG, sym_mask);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
     if (!dG) {

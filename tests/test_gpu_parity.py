@@ -205,3 +205,26 @@ def test_current_continuity_on_gpu(F):
     inner = (y > 0) & (y < mesh.ny - 1)
     expect = (2j * 1e-6 * Gl[0]).real
     assert np.abs(out[inner] - expect[inner]).max() <= 1e-9 * np.abs(J[0]).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_ff"])
+def test_symmetric_updates_match_full_updates(F, precision):
+    # closed-form leads: A = A^T, so U is computed on one triangle and R
+    # (anti-Hermitian) too; passing the same Sigma explicitly computes every
+    # entry.  Both must agree to rounding and with the dense definition.
+    import torch
+    mesh = W.Mesh(30, 44, 9, 1.0, 0.2, -1.0, 1.0, 66)
+    Es = W.energy_grid(0.7, 7.3, 3)
+    P = problem.MeshProblem.from_mesh(mesh)
+    sig = np.stack([P.lead_sigmas(E)[0] for E in Es])
+    f = F.Find.from_mesh(mesh, leaf=5, precision=precision)
+    a = [x.cpu().numpy() for x in f.solve_lesser(tcplx(Es))]
+    b = [x.cpu().numpy() for x in f.solve_lesser(tcplx(Es), sigmaL=tcplx(sig), sigmaR=tcplx(sig))]
+    f.close()
+    # computing one triangle of U moves results by rounding only (measured
+    # 7e-12 on a 64x128 mesh): both forms are held to the path's bar
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    for k in range(3):
+        for name, x, y in zip(("diagG", "diagGl", "J"), a, b):
+            assert rel(x[k], y[k]) <= tol, (name, k, rel(x[k], y[k]))
+        check((a[0][k], a[1][k], a[2][k]), dense_ref(mesh, Es[k]), tol=tol)
