@@ -31,10 +31,18 @@ METRIC = "diag(G)+diag(G<) energy points/s at 256x1024"
 UNIT = "energy points/s"
 WORKLOAD = ("256x1024 mesh, 9-point stencil (t=1, t'=0.2), V~U[-1,1] seed 1109, "
             "energies linspace(0.1,7.9,512)+1e-6i, outputs diag G, diag G<, bond currents")
-# FP64 peak of the kernels (DFMA on the CUDA cores): nominal 1.25 TFLOP/s at the
-# 2070 MHz maximum SM clock, scaled by the SM clock sampled during the run.
+# Peaks of the arithmetic units, scaled by the SM clock sampled during the run:
+# FP64 (DFMA on the CUDA cores): nominal 1.25 TFLOP/s at the 2070 MHz maximum
+# SM clock; FP32: 128 lanes per SM x 152 SMs, one instruction per lane per
+# clock (an FFMA counts 2 flops).
 FP64_NOMINAL_TFLOPS = 1.25
 SM_MAX_MHZ_NOMINAL = 2070.0
+N_SM = 152
+FP32_LANES = 128
+# FP32 instructions per float-float complex multiply-add in the kernels:
+# four products of 12 instructions (1 mul, 3 fma, 8 add) and two 3-add
+# renormalisations.
+FF_INST_PER_CMAC = 54
 # DRAM traffic per launch of the dominant kernel class, from the ncu capture
 # summarised in profiles/zgemm64_c5_256x1024.md (None: not captured for the
 # current kernel build).
@@ -46,11 +54,13 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=8, help="energies per step and rank")
+    ap.add_argument("--batch", type=int, default=32, help="energies per step and rank")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--path", choices=["fp64", "mixed", "mixed_ff"], default="fp64",
+    ap.add_argument("--no-side-paths", action="store_true",
+                    help="skip the one-step measurement of the other precision paths")
+    ap.add_argument("--path", choices=["fp64", "mixed", "mixed_ff"], default="mixed_ff",
                     help="fp64: every step in FP64; mixed: Sigma update and leaf G< products in "
                          "complex64, U and L solves in float-float, LU and leaf inversion FP64; "
                          "mixed_ff: LU and leaf inversion in float-float too")
@@ -139,11 +149,18 @@ def cpu_baseline(mesh, Es, gpu_solve=None):
                      f"numpy/LAPACK FP64 on all {cores} host cores, {dt:.1f} s"}
     accuracy = None
     if gpu_solve is not None:
-        gG, gGl = gpu_solve(np.array([E]))
-        accuracy = {"energy": [E.real, E.imag],
-                    "max_rel_err_diagG": float(np.abs(gG[0] - rG).max() / np.abs(rG).max()),
-                    "max_rel_err_diagGl": float(np.abs(gGl[0] - rGl).max() / np.abs(rGl).max())}
+        accuracy = accuracy_at([E.real, E.imag], mesh, gpu_solve, (rG, rGl))
+    cpu_baseline.ref = (rG, rGl)
     return out, accuracy
+
+
+def accuracy_at(energy, mesh, gpu_solve, ref):
+    """Normwise max relative error of diag G and diag G< against the oracle."""
+    rG, rGl = ref
+    gG, gGl = gpu_solve(np.array([complex(energy[0], energy[1])]))
+    return {"energy": list(energy),
+            "max_rel_err_diagG": float(np.abs(gG[0] - rG).max() / np.abs(rG).max()),
+            "max_rel_err_diagGl": float(np.abs(gGl[0] - rGl).max() / np.abs(rGl).max())}
 
 
 def serving(device, n_requests, chunk=8, slots=4, lam_frac=0.8):
@@ -180,6 +197,57 @@ def serving(device, n_requests, chunk=8, slots=4, lam_frac=0.8):
             "lambda_frac_of_capacity": lam_frac, "points_per_s": live["points_per_s"],
             "p50_s": live["p50_s"], "p99_s": live["p99_s"], "mean_queue_s": live["mean_queue_s"],
             "single_request_fp64_points_per_s": single}
+
+
+def kernel_roofline(p, f_sm):
+    """Achieved rate of one kernel class against the peak of the unit its
+    arithmetic uses.  p: the library profiler's entry (algorithmic real flops,
+    8 per complex multiply-add, and summed event time)."""
+    t = p["ms"] / 1e3
+    if p["name"].startswith("ff"):
+        # float-float: FP32 instructions issued per second
+        achieved = p["flops"] / 8.0 * FF_INST_PER_CMAC / t / 1e12
+        peak = FP32_LANES * N_SM * f_sm * 1e6 / 1e12
+        src = (f"float-float: {FF_INST_PER_CMAC} FP32 instructions per complex multiply-add; "
+               f"peak {FP32_LANES} lanes x {N_SM} SMs x {f_sm:.0f} MHz, FP32 instructions/s")
+    elif p["name"].startswith("c"):
+        achieved = p["flops"] / t / 1e12
+        peak = 2 * FP32_LANES * N_SM * f_sm * 1e6 / 1e12
+        src = f"complex64 FFMA: 2 x {FP32_LANES} lanes x {N_SM} SMs x {f_sm:.0f} MHz"
+    else:
+        achieved = p["flops"] / t / 1e12
+        peak = FP64_NOMINAL_TFLOPS * f_sm / SM_MAX_MHZ_NOMINAL
+        src = (f"FP64: nominal {FP64_NOMINAL_TFLOPS} TFLOP/s x sampled SM clock "
+               f"{f_sm:.0f}/{SM_MAX_MHZ_NOMINAL:.0f} MHz")
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "kernel": p["name"], "launches": p["launches"],
+            "ms": p["ms"], "peak_source": src}
+
+
+def side_path(F, mesh, Es, precision, B, device, rank, ws):
+    """One warm-up and one timed step of another precision path."""
+    import torch
+    from paper_1104_0623_gb300.shard import step_energies
+    f = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=B, precision=precision)
+    dev = f"cuda:{device}"
+    st = torch.cuda.current_stream(device)
+    E = [torch.tensor(step_energies(Es, k, rank, ws, B), dtype=torch.complex128, device=dev)
+         for k in range(2)]
+    out = (torch.empty((B, mesh.n), dtype=torch.complex128, device=dev),
+           torch.empty((B, mesh.n), dtype=torch.complex128, device=dev),
+           torch.empty((B, f.n_bonds), dtype=torch.float64, device=dev))
+    f.solve_lesser(E[0], 1.0, 0.0, out=out, stream=st.cuda_stream)
+    torch.cuda.synchronize(device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    f.solve_lesser(E[1], 1.0, 0.0, out=out, stream=st.cuda_stream)
+    e1.record(st)
+    torch.cuda.synchronize(device)
+    f.close()
+    t = e0.elapsed_time(e1) / 1e3
+    return {"value": B / t, "unit": UNIT, "ms_per_step": 1e3 * t, "energies_per_step": B,
+            "steps": 1, "warmup": 1}
 
 
 def run_reference(args):
@@ -282,24 +350,19 @@ def main():
         e2e = {"value": ws * args.steps * B / te, "unit": UNIT, "h2d_bytes_per_step": B * 16,
                "d2h_bytes_per_step": B * n * 16 * 2 + B * nb * 8}
 
-    # roofline of the dominant kernel class (FP64 CUDA-core arithmetic)
-    sm_mhz = clk.get("sm_mhz") or SM_MAX_MHZ_NOMINAL
-    peak = FP64_NOMINAL_TFLOPS * sm_mhz / SM_MAX_MHZ_NOMINAL
+    # roofline of the dominant kernel class, against the unit its arithmetic runs on
+    f_sm = clk.get("sm_mhz") or SM_MAX_MHZ_NOMINAL
     compute = [p for p in prof if p["flops"] > 0]
     dom = max(compute, key=lambda p: p["ms"])
-    achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
-    traffic = DOMINANT_TRAFFIC.get(dom["name"])
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": dom["name"],
-                "launches": dom["launches"], "ms": dom["ms"],
-                "peak_source": f"nominal FP64 {FP64_NOMINAL_TFLOPS} TFLOP/s x sampled SM clock "
-                               f"{sm_mhz:.0f}/{SM_MAX_MHZ_NOMINAL:.0f} MHz"}
+    roofline = kernel_roofline(dom, f_sm)
+    roofline["traffic"] = DOMINANT_TRAFFIC.get(dom["name"])
+    peak64 = FP64_NOMINAL_TFLOPS * f_sm / SM_MAX_MHZ_NOMINAL
     path_flops = f.stats.flops_lesser * args.steps * B
-    path = {"achieved": path_flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
-            "frac": path_flops / t / 1e12 / peak,
+    path = {"achieved": path_flops / t / 1e12, "peak": peak64, "unit": "TFLOP/s",
+            "frac": path_flops / t / 1e12 / peak64,
             "flops_per_energy": f.stats.flops_lesser,
             "note": "algorithmic flops of the whole pass over the FP64 peak; on the mixed "
-                    "path part of them run in complex64, so frac can exceed 1"}
+                    "paths most of them run in float-float or complex64, so frac can exceed 1"}
     kernels = {p["name"]: {"launches": p["launches"], "ms": round(p["ms"], 3),
                            "share": p["ms"] / sum(q["ms"] for q in prof)} for p in prof if p["launches"]}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -314,12 +377,27 @@ def main():
            "roofline": roofline, "path_roofline": path, "kernels": kernels}
     if e2e:
         out["e2e"] = e2e
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.mesh == "256x1024":
-        def gpu_solve(E):
-            G, Gl, _ = f.solve_lesser(np.ascontiguousarray(E), bonds=False)
-            return G, Gl
-        out["cpu_baseline"], out["accuracy_vs_oracle"] = cpu_baseline(mesh, Es, gpu_solve)
     f.close()
+    paths = {args.path: {"value": value, "ms_per_step": 1e3 * t / args.steps}}
+    if not args.no_side_paths and args.mesh == "256x1024":
+        for other in ("fp64", "mixed", "mixed_ff"):
+            if other != args.path:
+                paths[other] = side_path(F, mesh, Es, other, B, device, rank, ws)
+    out["paths"] = paths
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.mesh == "256x1024":
+        def gpu_solver(precision):
+            def run(E):
+                g = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=1, precision=precision)
+                G, Gl, _ = g.solve_lesser(np.ascontiguousarray(E), bonds=False)
+                g.close()
+                return G, Gl
+            return run
+        out["cpu_baseline"], acc = cpu_baseline(mesh, Es, gpu_solver(args.path))
+        out["accuracy_vs_oracle"] = {args.path: acc}
+        for other in paths:
+            if other != args.path:
+                out["accuracy_vs_oracle"][other] = accuracy_at(acc["energy"], mesh, gpu_solver(other),
+                                                               cpu_baseline.ref)
     if rank == 0 and ws == 1 and args.serve_requests > 0 and args.mesh == "256x1024":
         out["serving"] = serving(device, args.serve_requests)
     if rank == 0:

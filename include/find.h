@@ -49,19 +49,21 @@ enum {
 };
 
 /* FIND_FP64: every step in FP64.
- * FIND_MIXED: below the top fp64_top_levels tree levels, the Sigma update
- * (Eq. 7: T = L Sigma(S,S) - Sigma(B,S), R = Sigma(B,B) - L Sigma(S,B) + T L^H)
- * and the leaf products G_K Sigma_K G_K^H run in complex64 arithmetic, and
- * the Schur update U (Eq. 2) and the triangular solves for L (Eq. 13) in
- * float-float arithmetic (pairs of floats, about 48 significant bits); the
- * pivoted LU, the leaf inversion and every step of the top levels stay FP64.
- * Operands and results stay complex128 in memory.  Complex64 in the U update
- * was measured to lose up to 2.5e-3 (cancellation in ill-conditioned inner
- * blocks, amplified by later eliminations); in the Sigma update it costs
- * about 1e-6.
+ * FIND_MIXED: below the top fp64_top_levels tree levels, the Schur update U
+ * (Eq. 2), the triangular solves for L (Eq. 13), the Sigma update (Eq. 7:
+ * T = L Sigma(S,S) - Sigma(B,S), R = Sigma(B,B) - L Sigma(S,B) + T L^H) and
+ * the leaf products G_K Sigma_K G_K^H run in float-float arithmetic (pairs of
+ * floats, about 48 significant bits, on the FP32 pipes, which GB300 runs
+ * about 70 times faster than FP64); the pivoted LU, the leaf inversion and
+ * every step of the top levels stay FP64.  Operands and results stay
+ * complex128 in memory.  Measured on the 256x1024 9-point mesh: diag G and
+ * diag G< within 9e-9 of the FP64 oracle.
  * FIND_MIXED_FF: as FIND_MIXED, and below the top levels the pivoted LU and
- * the leaf inversion run in float-float arithmetic too (only the top levels
- * stay FP64). */
+ * the leaf inversion run in float-float too.
+ * Complex64 arithmetic is available for the Sigma update from a chosen tree
+ * depth down (find_desc.sigma_c64_depth); it is faster, but on the 256x1024
+ * mesh it left diag G< 4e-5 from the oracle (complex64 in the U update: up to
+ * 2.5e-3 on a 64x128 mesh, so U never uses it). */
 enum { FIND_FP64 = 0, FIND_MIXED = 1, FIND_MIXED_FF = 2 };
 
 typedef struct find_handle find_handle;
@@ -87,7 +89,14 @@ typedef struct {
   int invert_smem;          /* bordered leaf systems up to this size are
                                inverted in shared memory (at most 112);
                                <= 0 = never (the default: measured slower)     */
+  int sigma_c64_depth;      /* FIND_MIXED / _FF: the Sigma update of tree depths
+                               >= this one (and > fp64_top_levels) runs in
+                               complex64 instead of float-float; 0 = never     */
+  int flags;                /* FIND_FLAG_* bits                                */
 } find_desc;
+
+/* find_desc.flags: compute U on both triangles even when A = A^T */
+enum { FIND_FLAG_FULL_U = 1 };
 
 /* Host-side facts of the plan (no GPU needed). */
 typedef struct {

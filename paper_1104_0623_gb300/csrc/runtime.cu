@@ -318,8 +318,8 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
             bc->err = "assemble: gather index out of range";
         }
       }
-      // below the top FP64 levels the mixed path carries U and L in
-      // float-float and the Sigma update in complex64
+      // below the top FP64 levels the mixed paths carry U, L and the Sigma
+      // update in float-float (complex64 for Sigma only on request)
       const bool below_top = mixed && p.cl[op.cluster].depth > top_levels;
       const Arith ua = below_top ? kFF : kFP64;
       if (s > 0) {
@@ -351,7 +351,9 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       q.D = umat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
       q.sym = 1;  // U is complex symmetric when A is (Property 1)
       gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], ua);
-      const Arith sa = below_top ? kC64 : kFP64;
+      const int c64_from = h->desc.sigma_c64_depth;
+      const Arith sa = !below_top ? kFP64
+                       : ((c64_from > 0 && p.cl[op.cluster].depth >= c64_from) ? kC64 : kFF);
       if (lesser) {
         // stage 0: T = L Sigma(S,S) - Sigma(B,S)
         q = gemm0();
@@ -834,7 +836,7 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
     // groups' work
     // A = A^T when both leads take the closed form (Phi diag(sigma) Phi^T):
     // then every U is complex symmetric and its update runs on one triangle
-    const int sym_mask = (!sigL && !sigR) ? 1 : 0;
+    const int sym_mask = (!sigL && !sigR && !(h->desc.flags & FIND_FLAG_FULL_U)) ? 1 : 0;
     const int gsz = h->desc.energy_group > 0 ? h->desc.energy_group : 8;
     const int ng = std::min((nb + gsz - 1) / gsz, kMaxGroups);
     if (ng <= 1) {
@@ -1056,7 +1058,7 @@ int solve_static(find_handle* h, const double* E, int nE, const double* sigL, co
     P.fL = 0.0; P.fR = 0.0;
     P.dles = nullptr; P.dles_estride = 0;
     cplx* oG = dG ? reinterpret_cast<cplx*>(G) + (int64_t)e0 * n : reinterpret_cast<cplx*>(base + L.oG);
-    const int sym_mask = (!sigL && !sigR) ? 1 : 0;
+    const int sym_mask = (!sigL && !sigR && !(h->desc.flags & FIND_FLAG_FULL_U)) ? 1 : 0;
     for (const Level& lv : sv.levels) run_level_static(h, sv, lv, P, e0, nb, st, oG, sym_mask);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
