@@ -61,9 +61,10 @@ def parse():
     ap.add_argument("--no-side-paths", action="store_true",
                     help="skip the one-step measurement of the other precision paths")
     ap.add_argument("--path", choices=["fp64", "mixed", "mixed_ff"], default="mixed_ff",
-                    help="fp64: every step in FP64; mixed: Sigma update and leaf G< products in "
-                         "complex64, U and L solves in float-float, LU and leaf inversion FP64; "
-                         "mixed_ff: LU and leaf inversion in float-float too")
+                    help="fp64: every step in FP64; mixed: below the two top tree levels the "
+                         "U and Sigma updates, the solves for L and the leaf G< products in "
+                         "float-float, LU and leaf inversion FP64; mixed_ff: LU and leaf "
+                         "inversion in float-float too")
     ap.add_argument("--serve-requests", type=int, default=6,
                     help="requests of the serving scenario (0 skips it)")
     ap.add_argument("--mesh", default="256x1024",

@@ -93,10 +93,22 @@ typedef struct {
                                >= this one (and > fp64_top_levels) runs in
                                complex64 instead of float-float; 0 = never     */
   int flags;                /* FIND_FLAG_* bits                                */
+  int gemm_small_max;       /* a Schur-update or leaf product whose larger
+                               output side is at most this runs on 32x32
+                               tiles, a larger one on 64x64 tiles (a tuning
+                               knob; results do not depend on it); 0 = 32      */
 } find_desc;
 
-/* find_desc.flags: compute U on both triangles even when A = A^T */
-enum { FIND_FLAG_FULL_U = 1 };
+/* find_desc.flags.  With the closed-form leads A = A^T, so every U is complex
+   symmetric (Property 1) and its update can be computed on one triangle and
+   mirrored.  That halves the U products but carries a larger rounding error:
+   at 256x1024 the mirrored FP64 results were 3-10 times further from the
+   exact values than with both triangles computed.  Default: both triangles on
+   FIND_FP64, one triangle on the mixed paths (whose float-float rounding
+   dominates).
+     FIND_FLAG_FULL_U  both triangles on every path
+     FIND_FLAG_SYM_U   one triangle on FIND_FP64 too (ignored with FULL_U)  */
+enum { FIND_FLAG_FULL_U = 1, FIND_FLAG_SYM_U = 2 };
 
 /* Host-side facts of the plan (no GPU needed). */
 typedef struct {

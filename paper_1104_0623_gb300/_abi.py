@@ -20,6 +20,7 @@ FIND_FP64 = 0
 FIND_MIXED = 1
 FIND_MIXED_FF = 2
 FIND_FLAG_FULL_U = 1
+FIND_FLAG_SYM_U = 2
 
 STATUS_NAMES = {0: "FIND_OK", 1: "FIND_EINVAL", 2: "FIND_ENOMEM", 3: "FIND_ESINGULAR",
                 4: "FIND_ETIMEOUT", 5: "FIND_ECUDA"}
@@ -36,7 +37,8 @@ class find_desc(ctypes.Structure):
                 ("leaf", ctypes.c_int), ("precision", ctypes.c_int), ("device", ctypes.c_int),
                 ("max_batch", ctypes.c_int), ("fp64_top_levels", ctypes.c_int),
                 ("energy_group", ctypes.c_int), ("invert_smem", ctypes.c_int),
-                ("sigma_c64_depth", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("sigma_c64_depth", ctypes.c_int), ("flags", ctypes.c_int),
+                ("gemm_small_max", ctypes.c_int)]
 
 
 class find_plan_stats(ctypes.Structure):

@@ -164,9 +164,9 @@ int64_t leaf_slot_elems(const findgb::LeafOp& op, bool lesser) {
 
 // Adds one GEMM op to a stage, assigning its tiles to the small or big class.
 void add_gemm(findgb::GemmOp g, std::vector<findgb::GemmOp>& ops, std::vector<int>* maps,
-              Stage* st, Arith arith) {
+              Stage* st, Arith arith, int small_max) {
   if (g.m == 0 || g.n == 0) return;
-  bool is_big = std::max(g.m, g.n) > 32;
+  bool is_big = std::max(g.m, g.n) > small_max;
   const int cls = 2 * (int)arith + (is_big ? 1 : 0);
   st->fl[cls] += 8.0 * g.m * g.n * (double)(g.k + (g.A2 ? g.k2 : 0));
   int bm = is_big ? 64 : 32;
@@ -233,11 +233,15 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
   const bool ff_all = h->desc.precision == FIND_MIXED_FF;
   // shared-memory inversion only on request: measured slower than the
   // global-memory kernel (one 200 KB CTA per SM cannot hide its barriers)
+  const int small_max = h->desc.gemm_small_max > 0 ? h->desc.gemm_small_max : 32;
   const int inv_smem = h->desc.invert_smem <= 0 ? 0
                        : std::min(h->desc.invert_smem, findgb::invert_smem_max());
   const int top_levels = h->desc.fp64_top_levels < 0 ? 2 : h->desc.fp64_top_levels;
   auto gemm_ok = [&](const findgb::GemmOp& q) {
     if (!bc || q.m == 0 || q.n == 0) return;
+    // the kernels apply alpha as a sign
+    if ((q.alpha != 1.0 && q.alpha != -1.0) || (q.A2 && q.alpha2 != 1.0 && q.alpha2 != -1.0))
+      if (bc->err.empty()) bc->err = "gemm alpha must be +1 or -1";
     bc->block(q.A, q.m, q.k, q.lda, q.sa, batch, "gemm A");
     if (q.opb == 0) bc->block(q.B, q.k, q.n, q.ldb, q.sb, batch, "gemm B");
     else bc->block(q.B, q.n, q.k, q.ldb, q.sb, batch, "gemm B^H");
@@ -350,7 +354,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       q.C = M + (int64_t)s * n + s; q.ldc = n; q.sc = escr; q.beta = 1.0;
       q.D = umat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
       q.sym = 1;  // U is complex symmetric when A is (Property 1)
-      gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], ua);
+      gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], ua, small_max);
       const int c64_from = h->desc.sigma_c64_depth;
       const Arith sa = !below_top ? kFP64
                        : ((c64_from > 0 && p.cl[op.cluster].depth >= c64_from) ? kC64 : kFF);
@@ -362,7 +366,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         q.B = Sg; q.ldb = n; q.sb = escr;
         q.C = Sg + (int64_t)s * n; q.ldc = n; q.sc = escr; q.beta = -1.0;
         q.D = T; q.ldd = s; q.sd = escr;
-        gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], sa);
+        gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], sa, small_max);
         // stage 1: R = Sigma(B,B) - L Sigma(S,B) + T L^H     (Eq. 7)
         q = gemm0();
         q.m = b; q.n = b; q.k = s; q.k2 = s;
@@ -377,7 +381,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         // mutually consistent: mirroring one triangle was measured to raise
         // the diag G< error from 1e-6 to 1e-2 (complex64) and from 5e-15 to
         // 3e-11 (FP64), so R is computed in full
-        gemm_ok(q); add_gemm(q, g[1], maps[1], &lv.st[1], sa);
+        gemm_ok(q); add_gemm(q, g[1], maps[1], &lv.st[1], sa, small_max);
       }
     }
     lv.nops = (int)ops.size();
@@ -476,14 +480,14 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         // keeps the mixed paths' G< error near that of the complex64 Sigma
         // update alone (complex64 here reached 1e-5 on a 64x128 mesh)
         const Arith la = (mixed && p.cl[op.cluster].depth > top_levels) ? kFF : kFP64;
-        gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], la);
+        gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], la, small_max);
         // Q = P G_K^H = G<_K(C, :)
         q = gemm0();
         q.m = op.c; q.n = n; q.k = n;
         q.A = P; q.lda = n; q.sa = escr;
         q.B = M; q.ldb = n; q.sb = escr; q.opb = 1;
         q.D = Q; q.ldd = n; q.sd = escr;
-        gemm_ok(q); add_gemm(q, g[1], maps[1], &lv.st[1], la);
+        gemm_ok(q); add_gemm(q, g[1], maps[1], &lv.st[1], la, small_max);
       }
       findgb::ExtractOp x;
       x.K = M;
@@ -651,6 +655,14 @@ const char* kClassNames[kClasses] = {"lead",    "assemble", "invert",   "lu",   
                                      "ffgemm32", "ffgemm64", "fftrsm",  "fflu",     "ffinvert"};
 // profiler class of each GEMM launch class 2 * arith + big
 const int kGemmClass[6] = {5, 6, 8, 9, 10, 11};
+
+// 1 when every U update runs on one triangle (closed-form leads make
+// A = A^T): by default on the mixed paths only, see FIND_FLAG_SYM_U.
+int sym_updates(const find_handle* h, const void* sigL, const void* sigR) {
+  if (sigL || sigR || (h->desc.flags & FIND_FLAG_FULL_U)) return 0;
+  if (h->desc.precision == FIND_FP64 && !(h->desc.flags & FIND_FLAG_SYM_U)) return 0;
+  return 1;
+}
 
 cudaEvent_t take_event(find_handle* h) {
   if (!h->ev_free.empty()) {
@@ -836,7 +848,7 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
     // groups' work
     // A = A^T when both leads take the closed form (Phi diag(sigma) Phi^T):
     // then every U is complex symmetric and its update runs on one triangle
-    const int sym_mask = (!sigL && !sigR && !(h->desc.flags & FIND_FLAG_FULL_U)) ? 1 : 0;
+    const int sym_mask = sym_updates(h, sigL, sigR);
     const int gsz = h->desc.energy_group > 0 ? h->desc.energy_group : 8;
     const int ng = std::min((nb + gsz - 1) / gsz, kMaxGroups);
     if (ng <= 1) {
@@ -1058,7 +1070,7 @@ int solve_static(find_handle* h, const double* E, int nE, const double* sigL, co
     P.fL = 0.0; P.fR = 0.0;
     P.dles = nullptr; P.dles_estride = 0;
     cplx* oG = dG ? reinterpret_cast<cplx*>(G) + (int64_t)e0 * n : reinterpret_cast<cplx*>(base + L.oG);
-    const int sym_mask = (!sigL && !sigR && !(h->desc.flags & FIND_FLAG_FULL_U)) ? 1 : 0;
+    const int sym_mask = sym_updates(h, sigL, sigR);
     for (const Level& lv : sv.levels) run_level_static(h, sv, lv, P, e0, nb, st, oG, sym_mask);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
@@ -1091,6 +1103,7 @@ int find_create(const find_desc* d, find_handle** out) {
     return fail(nullptr, FIND_EINVAL, "precision must be FIND_FP64, FIND_MIXED or FIND_MIXED_FF");
   if (d->stencil != 5 && d->stencil != 9) return fail(nullptr, FIND_EINVAL, "stencil must be 5 or 9");
   if (d->max_batch < 0) return fail(nullptr, FIND_EINVAL, "max_batch < 0");
+  if (d->gemm_small_max < 0) return fail(nullptr, FIND_EINVAL, "gemm_small_max < 0");
   find_handle* h = new (std::nothrow) find_handle();
   if (!h) return fail(nullptr, FIND_ENOMEM, "host allocation");
   h->desc = *d;

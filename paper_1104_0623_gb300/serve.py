@@ -61,19 +61,23 @@ class GpuBackend:
     """Plans are libfind handles; a chunk is one find_solve_lesser call with
     host outputs on the worker's stream."""
 
-    def __init__(self, device=0, precision="mixed", leaf=8, chunk=16):
+    def __init__(self, device=0, precision="mixed", leaf=8, chunk=16, tuner=None):
         import torch
 
         import paper_1104_0623_gb300 as F
         self.F, self.torch = F, torch
         self.device, self.precision, self.leaf, self.chunk = device, precision, leaf, chunk
+        self.tuner = tuner        # paper_1104_0623_gb300.tune.Tuner, or None for fixed knobs
 
     def new_stream(self):
         return self.torch.cuda.Stream(device=self.device)
 
-    def make_plan(self, mesh):
-        return self.F.Find.from_mesh(mesh, leaf=self.leaf, device=self.device, max_batch=self.chunk,
-                                     precision=self.precision)
+    def make_plan(self, mesh, energies=None):
+        params = {"leaf": self.leaf}
+        if self.tuner is not None and energies is not None:
+            params = self.tuner.tune(mesh, energies[:self.chunk], self.precision, self.chunk)
+        return self.F.Find.from_mesh(mesh, device=self.device, max_batch=self.chunk,
+                                     precision=self.precision, **params)
 
     def plan_bytes(self, plan):
         return plan.workspace_bytes(self.chunk, True)
@@ -108,14 +112,14 @@ class Server:
         self.t0 = None
 
     # -- plan cache
-    def _plan_for(self, mesh):
+    def _plan_for(self, mesh, energies=None):
         """Cached plan of a mesh, or None if its footprint does not fit now.
         Called with self.lock held."""
         key = mesh_key(mesh)
         if key in self.plans:
             self.plans.move_to_end(key)
             return self.plans[key]
-        plan = self.backend.make_plan(mesh)
+        plan = self.backend.make_plan(mesh, energies)
         need = self.backend.plan_bytes(plan)
         used = sum(p[1] for p in self.plans.values())
         for k in list(self.plans.keys()):
@@ -135,7 +139,7 @@ class Server:
         """Admit pending requests in arrival order while slots and memory allow."""
         while self.pending and len(self.active) < self.slots:
             req = self.pending[0]
-            entry = self._plan_for(req.mesh)
+            entry = self._plan_for(req.mesh, req.energies)
             if entry is None:
                 if not self.active:
                     raise RuntimeError(f"request {req.rid} does not fit the device memory budget")
@@ -217,6 +221,19 @@ class Server:
         for p in self.plans.values():
             self.backend.close_plan(p[0])
         self.plans.clear()
+
+
+def solve_ragged(items, backend, slots=4, chunk=16):
+    """A ragged batch: several meshes, each with its own energy grid, solved
+    together (all admitted at once, chunks interleaved over `slots` streams).
+    items: list of (mesh, energies); returns [(diagG, diagG<)] in item order."""
+    srv = Server(backend, slots=slots, chunk=chunk)
+    try:
+        res = srv.run([Request(k, 0.0, m, np.asarray(e, dtype=np.complex128))
+                       for k, (m, e) in enumerate(items)])
+    finally:
+        srv.close()
+    return [(r.diagG, r.diagGl) for r in res]
 
 
 def summarize(results: List[Result]):

@@ -217,7 +217,7 @@ def test_symmetric_updates_match_full_updates(F, precision):
     Es = W.energy_grid(0.7, 7.3, 3)
     P = problem.MeshProblem.from_mesh(mesh)
     sig = np.stack([P.lead_sigmas(E)[0] for E in Es])
-    f = F.Find.from_mesh(mesh, leaf=5, precision=precision)
+    f = F.Find.from_mesh(mesh, leaf=5, precision=precision, sym_u=True)
     a = [x.cpu().numpy() for x in f.solve_lesser(tcplx(Es))]
     b = [x.cpu().numpy() for x in f.solve_lesser(tcplx(Es), sigmaL=tcplx(sig), sigmaR=tcplx(sig))]
     f.close()

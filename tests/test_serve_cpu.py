@@ -22,7 +22,7 @@ class FakeBackend:
     def new_stream(self):
         return None
 
-    def make_plan(self, mesh):
+    def make_plan(self, mesh, energies=None):
         return ("plan", mesh_key(mesh), mesh.nx * mesh.ny)
 
     def plan_bytes(self, plan):
