@@ -84,6 +84,11 @@ __device__ __forceinline__ void df_split(double x, float& h, float& l) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7ffull);
   if (e < 1023 - 126 || e > 1023 + 127) {
+    if ((b << 1) == 0ull) {  // +-0 (padding, the zeros of sparse blocks): the
+      h = __uint_as_float((unsigned int)(b >> 32));  // same words as below
+      l = 0.0f;
+      return;
+    }
     h = __double2float_rn(x);
     l = __double2float_rn(x - (double)h);
     return;
@@ -116,10 +121,19 @@ __device__ __forceinline__ void df_norm(float& h, float& l) {
   l = l - (t - h);
   h = t;
 }
-__device__ __forceinline__ float4 df_load(cplx v, double a) {
+__device__ __forceinline__ float fneg_if(float x, bool neg) {
+  return __int_as_float(__float_as_int(x) ^ (neg ? (int)0x80000000 : 0));
+}
+// v (negated when neg) in float-float; df_split is odd in its argument, so
+// negating the words afterwards is exact and needs no FP64 instruction
+__device__ __forceinline__ float4 df_load(cplx v, bool neg) {
   float4 r;
-  df_split(a < 0.0 ? -v.x : v.x, r.x, r.y);
-  df_split(a < 0.0 ? -v.y : v.y, r.z, r.w);
+  df_split(v.x, r.x, r.y);
+  df_split(v.y, r.z, r.w);
+  r.x = fneg_if(r.x, neg);
+  r.y = fneg_if(r.y, neg);
+  r.z = fneg_if(r.z, neg);
+  r.w = fneg_if(r.w, neg);
   return r;
 }
 // c + a * b, complex float-float
@@ -254,6 +268,7 @@ struct GA;
 template <>
 struct GA<false> {
   typedef cplx T;
+  typedef double M;  // pivot magnitude
   __device__ __forceinline__ static T from(cplx v) { return v; }
   __device__ __forceinline__ static cplx to(T v) { return v; }
   __device__ __forceinline__ static double mag(T v) { return fabs(v.x) + fabs(v.y); }
@@ -266,9 +281,10 @@ struct GA<false> {
 template <>
 struct GA<true> {
   typedef float4 T;
-  __device__ __forceinline__ static T from(cplx v) { return df_load(v, 1.0); }
+  typedef float M;   // pivot magnitude: compared in float, no FP64 instruction
+  __device__ __forceinline__ static T from(cplx v) { return df_load(v, false); }
   __device__ __forceinline__ static cplx to(T v) { return df_wide(v); }
-  __device__ __forceinline__ static double mag(T v) { return (double)(fabsf(v.x) + fabsf(v.z)); }
+  __device__ __forceinline__ static float mag(T v) { return fabsf(v.x) + fabsf(v.z); }
   __device__ __forceinline__ static T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
   __device__ __forceinline__ static T scale(T a, T b) {
     T r = df_cfma(a, b, make_float4(0.f, 0.f, 0.f, 0.f));
@@ -288,27 +304,28 @@ struct GA<true> {
 // Block-wide argmax of mag over rows k..s-1 of column k (largest magnitude,
 // first index on ties); returns the row.
 template <class X, class T>
-__device__ __forceinline__ int pivot_row(const T* a, int ld, int k, int s, double* red_v, int* red_i,
+__device__ __forceinline__ int pivot_row(const T* a, int ld, int k, int s, typename X::M* red_v, int* red_i,
                                          int* sh_p) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  double best = -1.0;
+  typedef typename X::M M;
+  M best = M(-1);
   int bi = INT_MAX;
   for (int i = k + tid; i < s; i += blockDim.x) {
-    double mg = X::mag(a[(int64_t)i * ld + k]);
+    M mg = X::mag(a[(int64_t)i * ld + k]);
     if (mg > best) { best = mg; bi = i; }
   }
   for (int off = 16; off > 0; off >>= 1) {
-    double ob = __shfl_down_sync(0xffffffffu, best, off);
+    M ob = __shfl_down_sync(0xffffffffu, best, off);
     int oi = __shfl_down_sync(0xffffffffu, bi, off);
     if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
   }
   if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
   __syncthreads();
   if (warp == 0) {
-    best = lane < nwarp ? red_v[lane] : -1.0;
+    best = lane < nwarp ? red_v[lane] : M(-1);
     bi = lane < nwarp ? red_i[lane] : INT_MAX;
     for (int off = 16; off > 0; off >>= 1) {
-      double ob = __shfl_down_sync(0xffffffffu, best, off);
+      M ob = __shfl_down_sync(0xffffffffu, best, off);
       int oi = __shfl_down_sync(0xffffffffu, bi, off);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
@@ -328,7 +345,7 @@ constexpr int kInvThreads = 512;
 template <class X, class T>
 __device__ void gauss_jordan(T* a, int ld, int s, T* colk, T* rowk, int* piv, int* status,
                              int energy) {
-  __shared__ double red_v[32];
+  __shared__ typename X::M red_v[32];
   __shared__ int red_i[32];
   __shared__ int sh_p;
   __shared__ T sh_pinv;
@@ -481,7 +498,7 @@ __global__ void __launch_bounds__(kInvThreads) k_lu(const InvOp* __restrict__ op
   int* piv = op.piv + (int64_t)e * op.piv_estride;
   extern __shared__ double2 lu_smem[];
   T* rowk = reinterpret_cast<T*>(lu_smem);
-  __shared__ double red_v[32];
+  __shared__ typename X::M red_v[32];
   __shared__ int red_i[32];
   __shared__ int sh_p;
   __shared__ T sh_pinv;
@@ -531,7 +548,9 @@ struct Cx;
 template <>
 struct Cx<double2> {
   __device__ __forceinline__ static double2 zero() { return make_double2(0.0, 0.0); }
-  __device__ __forceinline__ static double2 load(cplx v, double a) { return make_double2(v.x * a, v.y * a); }
+  __device__ __forceinline__ static double2 load(cplx v, bool neg) {
+    return neg ? make_double2(-v.x, -v.y) : v;
+  }
   __device__ __forceinline__ static double2 fma(double2 a, double2 b, double2 c) { return cfma(a, b, c); }
   __device__ __forceinline__ static cplx wide(double2 v) { return v; }
   __device__ __forceinline__ static void renorm(double2&) {}
@@ -540,8 +559,8 @@ struct Cx<double2> {
 template <>
 struct Cx<float2> {
   __device__ __forceinline__ static float2 zero() { return make_float2(0.f, 0.f); }
-  __device__ __forceinline__ static float2 load(cplx v, double a) {
-    return make_float2((float)(v.x * a), (float)(v.y * a));
+  __device__ __forceinline__ static float2 load(cplx v, bool neg) {
+    return make_float2(fneg_if((float)v.x, neg), fneg_if((float)v.y, neg));
   }
   __device__ __forceinline__ static float2 fma(float2 a, float2 b, float2 c) {
     c.x = fmaf(a.x, b.x, c.x);
@@ -557,7 +576,7 @@ struct Cx<float2> {
 template <>
 struct Cx<float4> {
   __device__ __forceinline__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-  __device__ __forceinline__ static float4 load(cplx v, double a) { return df_load(v, a); }
+  __device__ __forceinline__ static float4 load(cplx v, bool neg) { return df_load(v, neg); }
   __device__ __forceinline__ static float4 fma(float4 a, float4 b, float4 c) { return df_cfma(a, b, c); }
   __device__ __forceinline__ static cplx wide(float4 v) { return df_wide(v); }
   __device__ __forceinline__ static void renorm(float4& v) {
@@ -602,7 +621,7 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4), (sizeof(CT) == 16 && BM =
     if (A == nullptr || K == 0) continue;
     const int lda = pass ? op.lda2 : op.lda, ldb = pass ? op.ldb2 : op.ldb;
     const int opb = pass ? op.opb2 : op.opb;
-    const double alpha = pass ? op.alpha2 : op.alpha;
+    const bool neg = (pass ? op.alpha2 : op.alpha) < 0.0;  // alpha is +1 or -1
     A += (int64_t)e * (pass ? op.sa2 : op.sa);
     B += (int64_t)e * (pass ? op.sb2 : op.sb);
     for (int k0 = 0; k0 < K; k0 += BK) {
@@ -610,23 +629,25 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4), (sizeof(CT) == 16 && BM =
         int i = idx / BK, kk = idx % BK;
         int gi = m0 + i, gk = k0 + kk;
         cplx v = (gi < M && gk < K) ? A[(int64_t)gi * lda + gk] : cmk(0, 0);
-        As[kk][i] = X::load(v, alpha);
+        As[kk][i] = X::load(v, neg);
       }
       if (opb == 0) {
         for (int idx = threadIdx.x; idx < BK * BN; idx += NT) {
           int kk = idx / BN, j = idx % BN;
           int gk = k0 + kk, gj = n0 + j;
-          Bs[kk][j] = X::load((gk < K && gj < N) ? B[(int64_t)gk * ldb + gj] : cmk(0, 0), 1.0);
+          Bs[kk][j] = X::load((gk < K && gj < N) ? B[(int64_t)gk * ldb + gj] : cmk(0, 0), false);
         }
       } else {
         for (int idx = threadIdx.x; idx < BK * BN; idx += NT) {
           int j = idx / BK, kk = idx % BK;
           int gk = k0 + kk, gj = n0 + j;
-          Bs[kk][j] = X::load((gk < K && gj < N) ? cconj(B[(int64_t)gj * ldb + gk]) : cmk(0, 0), 1.0);
+          Bs[kk][j] = X::load((gk < K && gj < N) ? cconj(B[(int64_t)gj * ldb + gk]) : cmk(0, 0), false);
         }
       }
       __syncthreads();
-#pragma unroll
+      // the float-float step is ~800 instructions: unrolling the k loop
+      // as well would outgrow the instruction cache
+#pragma unroll(sizeof(CT) == 16 ? 1 : BK)
       for (int kk = 0; kk < BK; ++kk) {
         CT av[4], bv[4];
 #pragma unroll
@@ -683,6 +704,10 @@ struct TrsmArith;
 template <>
 struct TrsmArith<false> {
   typedef cplx T;
+  __device__ __forceinline__ static T zero() { return cmk(0, 0); }
+  __device__ __forceinline__ static T shfl(T v, int src) {
+    return cmk(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+  }
   __device__ __forceinline__ static T in(cplx v) { return v; }
   __device__ __forceinline__ static cplx out(T v) { return v; }
   __device__ __forceinline__ static T mul(T a, cplx b) { return cmul(a, b); }
@@ -693,10 +718,15 @@ struct TrsmArith<false> {
 template <>
 struct TrsmArith<true> {
   typedef float4 T;
-  __device__ __forceinline__ static T in(cplx v) { return df_load(v, 1.0); }
+  __device__ __forceinline__ static T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  __device__ __forceinline__ static T shfl(T v, int src) {
+    return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                       __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+  }
+  __device__ __forceinline__ static T in(cplx v) { return df_load(v, false); }
   __device__ __forceinline__ static cplx out(T v) { return df_wide(v); }
   __device__ __forceinline__ static T mul(T a, cplx b) {
-    return df_cfma(a, df_load(b, 1.0), make_float4(0.f, 0.f, 0.f, 0.f));
+    return df_cfma(a, df_load(b, false), make_float4(0.f, 0.f, 0.f, 0.f));
   }
   __device__ __forceinline__ static T mul2(T a, T b) {
     T r = df_cfma(a, b, make_float4(0.f, 0.f, 0.f, 0.f));
@@ -712,12 +742,47 @@ struct TrsmArith<true> {
   }
 };
 
+constexpr int kTrsmW = 8;        // columns per panel
+constexpr int kTrsmRowsMax = 16; // rows per CTA at most
+constexpr int kPanelThreads = kTrsmW * kTrsmRowsMax;  // 4 whole warps
+static_assert(kPanelThreads % 32 == 0 && 32 % kTrsmW == 0, "panel lanes must tile warps");
+
+// Y(r, i) -= sum_{t < w} Y(r, j0 + t) * F(j0 + t, i) for rows r < rows and
+// columns i in [c0, c1), F the factor in a (leading dimension ld).  Threads
+// take (column, row group) pairs so that narrow updates still occupy the
+// block; each element sees the same operations in the same order as one
+// thread per column would give it.
+template <class X, class T>
+__device__ __forceinline__ void rank_update(T* Y, const cplx* a, int ld, int s, int rows, int j0,
+                                            int w, int c0, int c1, int tid, int nt) {
+  constexpr int W = kTrsmW;
+  const int C = c1 - c0;
+  if (C <= 0) return;
+  const int tpc = C >= nt ? 1 : max(1, min(rows, nt / C));  // threads per column
+  const int rpt = (rows + tpc - 1) / tpc;                   // rows per thread
+  for (int it = tid; it < C * tpc; it += nt) {
+    const int i = c0 + it / tpc, rg = it % tpc;
+    T u[W];
+#pragma unroll
+    for (int t = 0; t < W; ++t)
+      if (t < w) u[t] = X::in(a[(int64_t)(j0 + t) * ld + i]);
+    const int r1 = min(rows, (rg + 1) * rpt);
+    for (int r = rg * rpt; r < r1; ++r) {
+      T v = Y[r * s + i];
+#pragma unroll
+      for (int t = 0; t < W; ++t)
+        if (t < w) v = X::fms(Y[r * s + j0 + t], u[t], v);
+      Y[r * s + i] = v;
+    }
+  }
+}
+
 template <bool DF>
 __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
                                               const int* __restrict__ tile_op, int rb, int e_off) {
   typedef TrsmArith<DF> X;
   typedef typename X::T T;
-  constexpr int W = 8;  // columns per panel: one panel solve and one rank-W update per barrier pair
+  constexpr int W = kTrsmW;  // one panel solve and one rank-W update per barrier pair
   const TrsmOp& op = ops[tile_op[blockIdx.x]];
   const int e = blockIdx.y + e_off;
   const int s = op.s, ld = op.ld;
@@ -750,27 +815,19 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
       }
     }
     __syncthreads();
-    if (tid < rows) {  // the panel's own columns, one row per thread
-      T* y = Y + tid * s + j0;
+    if (tid < kPanelThreads) {  // the panel's own columns: W lanes per row, whole warps
+      const int r = tid / W, c = tid % W, grp = (tid & 31) & ~(W - 1);
+      const bool act = r < rows && c < w;
+      T yv = act ? Y[r * s + j0 + c] : X::zero();
       for (int t = 0; t < w; ++t) {
-        y[t] = X::mul2(y[t], dgl[t]);
-        for (int t2 = t + 1; t2 < w; ++t2) y[t2] = X::fms(y[t], pan[t][t2], y[t2]);
+        if (act && c == t) yv = X::mul2(yv, dgl[t]);
+        const T yt = X::shfl(yv, grp | t);  // column t of this row, final from here on
+        if (act && c > t) yv = X::fms(yt, pan[t][c], yv);
       }
+      if (act) Y[r * s + j0 + c] = yv;
     }
     __syncthreads();
-    for (int i = j0 + w + tid; i < s; i += nt) {  // rank-w update of the later columns
-      T u[W];
-#pragma unroll
-      for (int t = 0; t < W; ++t)
-        if (t < w) u[t] = X::in(a[(int64_t)(j0 + t) * ld + i]);
-      for (int r = 0; r < rows; ++r) {
-        T v = Y[r * s + i];
-#pragma unroll
-        for (int t = 0; t < W; ++t)
-          if (t < w) v = X::fms(Y[r * s + j0 + t], u[t], v);
-        Y[r * s + i] = v;
-      }
-    }
+    rank_update<X>(Y, a, ld, s, rows, j0, w, j0 + w, s, tid, nt);  // the later columns
     __syncthreads();
   }
   // backward: Z L = Y with L unit lower, panels of W columns right to left
@@ -781,25 +838,18 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
       if (t2 < t) pan[t][t2] = X::in(a[(int64_t)(j0 + t) * ld + j0 + t2]);
     }
     __syncthreads();
-    if (tid < rows) {
-      T* y = Y + tid * s + j0;
-      for (int t = w - 1; t > 0; --t)
-        for (int t2 = 0; t2 < t; ++t2) y[t2] = X::fms(y[t], pan[t][t2], y[t2]);
+    if (tid < kPanelThreads) {
+      const int r = tid / W, c = tid % W, grp = (tid & 31) & ~(W - 1);
+      const bool act = r < rows && c < w;
+      T yv = act ? Y[r * s + j0 + c] : X::zero();
+      for (int t = w - 1; t > 0; --t) {
+        const T yt = X::shfl(yv, grp | t);
+        if (act && c < t) yv = X::fms(yt, pan[t][c], yv);
+      }
+      if (act) Y[r * s + j0 + c] = yv;
     }
     __syncthreads();
-    for (int i = tid; i < j0; i += nt) {
-      T l[W];
-#pragma unroll
-      for (int t = 0; t < W; ++t)
-        if (t < w) l[t] = X::in(a[(int64_t)(j0 + t) * ld + i]);
-      for (int r = 0; r < rows; ++r) {
-        T v = Y[r * s + i];
-#pragma unroll
-        for (int t = 0; t < W; ++t)
-          if (t < w) v = X::fms(Y[r * s + j0 + t], l[t], v);
-        Y[r * s + i] = v;
-      }
-    }
+    rank_update<X>(Y, a, ld, s, rows, j0, w, 0, j0, tid, nt);  // the earlier columns
     __syncthreads();
   }
   // L = Z P: column j of the result is column perm[j] of Z
@@ -911,9 +961,9 @@ int invert_smem_max() { return kInvSmemMax; }
 constexpr int kTrsmSmem = 196608;
 
 int trsm_rows_per_block(int max_s) {
-  if (max_s <= 0) return 16;
+  if (max_s <= 0) return kTrsmRowsMax;
   int rb = (int)((kTrsmSmem - (int64_t)max_s * 4) / ((int64_t)max_s * sizeof(cplx)));
-  return rb < 1 ? 1 : (rb > 16 ? 16 : rb);
+  return rb < 1 ? 1 : (rb > kTrsmRowsMax ? kTrsmRowsMax : rb);
 }
 
 void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int max_s, int nE,
