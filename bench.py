@@ -36,6 +36,9 @@ WORKLOAD = ("256x1024 mesh, 9-point stencil (t=1, t'=0.2), V~U[-1,1] seed 1109, 
 # SM clock; FP32: 128 lanes per SM x 152 SMs, one instruction per lane per
 # clock (an FFMA counts 2 flops).
 FP64_NOMINAL_TFLOPS = 1.25
+# FP64 tensor (DMMA m8n8k4) rate measured on this GPU by a throwaway probe at
+# 2070 MHz; DFMA on the CUDA cores measured 1.006 TFLOP/s
+FP64_DMMA_MEASURED_TFLOPS = 1.049
 SM_MAX_MHZ_NOMINAL = 2070.0
 N_SM = 152
 FP32_LANES = 128
@@ -43,9 +46,11 @@ FP32_LANES = 128
 # four products of 12 instructions (1 mul, 3 fma, 8 add) and two 3-add
 # renormalisations.
 FF_INST_PER_CMAC = 54
-# DRAM traffic per launch of the dominant kernel class, from the ncu capture
-# summarised in profiles/zgemm64_c5_256x1024.md (None: not captured for the
-# current kernel build).
+# DRAM traffic per launch of the dominant kernel class (dram__bytes_read.sum +
+# dram__bytes_write.sum).  Empty: the launches of a class differ by tree level
+# and the ncu captures (profiles/) are of the 128x512 profiling case, where the
+# float-float GEMM moved 0.29-0.47 GB per 3.2-3.5 ms launch (DRAM ~1 % busy);
+# no per-launch figure of the bench's launches is claimed.
 DOMINANT_TRAFFIC = {}
 
 
@@ -67,6 +72,9 @@ def parse():
                          "inversion in float-float too")
     ap.add_argument("--serve-requests", type=int, default=6,
                     help="requests of the serving scenario (0 skips it)")
+    ap.add_argument("--serve-lambdas", default="0.8",
+                    help="comma-separated arrival rates of the serving scenario, as fractions "
+                         "of its measured capacity")
     ap.add_argument("--mesh", default="256x1024",
                     help="NXxNY of the 9-point mesh (smaller meshes only for profiling)")
     return ap.parse_args()
@@ -164,10 +172,11 @@ def accuracy_at(energy, mesh, gpu_solve, ref):
             "max_rel_err_diagGl": float(np.abs(gGl[0] - rGl).max() / np.abs(rGl).max())}
 
 
-def serving(device, n_requests, chunk=8, slots=4, lam_frac=0.8):
+def serving(device, n_requests, precision="mixed_ff", chunk=8, slots=4, lam_fracs=(0.8,)):
     """Serving scenario: requests from the c4 distribution (Nx~U{32..256},
-    Ny~U{32..1024}, 8-128 energies, 5-point), mixed path.  Capacity from a
-    closed loop; then Poisson arrivals at lam_frac x capacity; then the same
+    Ny~U{32..1024}, 8-128 energies, 5-point) on one of the mixed paths.
+    Capacity from a closed loop (all requests at t = 0); then, per entry of
+    lam_fracs, Poisson arrivals at that fraction of capacity; then the same
     requests one at a time on the plain FP64 path."""
     import torch
 
@@ -176,15 +185,20 @@ def serving(device, n_requests, chunk=8, slots=4, lam_frac=0.8):
     base = W.serving_stream(n_requests, rate_hz=1.0, seed=2011)
     pts = [len(r.energies) for r in base]
     closed = [Request(k, 0.0, r.mesh, r.energies) for k, r in enumerate(base)]
-    srv = Server(GpuBackend(device, "mixed", chunk=chunk), slots=slots, chunk=chunk)
+    srv = Server(GpuBackend(device, precision, chunk=chunk), slots=slots, chunk=chunk)
     cap = summarize(srv.run(closed))
     srv.close()
-    lam = lam_frac * cap["points_per_s"] / float(np.mean(pts))
-    stream = W.serving_stream(n_requests, rate_hz=lam, seed=2011)
-    reqs = [Request(k, r.arrival_s, r.mesh, r.energies) for k, r in enumerate(stream)]
-    srv = Server(GpuBackend(device, "mixed", chunk=chunk), slots=slots, chunk=chunk)
-    live = summarize(srv.run(reqs))
-    srv.close()
+    live = []
+    for frac in lam_fracs:
+        lam = frac * cap["points_per_s"] / float(np.mean(pts))
+        stream = W.serving_stream(n_requests, rate_hz=lam, seed=2011)
+        reqs = [Request(k, r.arrival_s, r.mesh, r.energies) for k, r in enumerate(stream)]
+        srv = Server(GpuBackend(device, precision, chunk=chunk), slots=slots, chunk=chunk)
+        sm = summarize(srv.run(reqs))
+        srv.close()
+        live.append({"lambda_frac_of_capacity": frac, "lambda_req_per_s": lam,
+                     "points_per_s": sm["points_per_s"], "p50_s": sm["p50_s"], "p99_s": sm["p99_s"],
+                     "mean_queue_s": sm["mean_queue_s"]})
     torch.cuda.synchronize(device)
     t = time.perf_counter()
     for r in base:
@@ -192,11 +206,13 @@ def serving(device, n_requests, chunk=8, slots=4, lam_frac=0.8):
         f.solve_lesser(np.ascontiguousarray(r.energies), bonds=False)
         f.close()
     single = sum(pts) / (time.perf_counter() - t)
-    return {"scenario": f"{n_requests} requests, c4 distribution (seed 2011), mixed path, "
+    first = live[0]
+    return {"scenario": f"{n_requests} requests, c4 distribution (seed 2011), {precision} path, "
                         f"{slots} slots, {chunk}-energy chunks",
-            "capacity_points_per_s": cap["points_per_s"], "lambda_req_per_s": lam,
-            "lambda_frac_of_capacity": lam_frac, "points_per_s": live["points_per_s"],
-            "p50_s": live["p50_s"], "p99_s": live["p99_s"], "mean_queue_s": live["mean_queue_s"],
+            "capacity_points_per_s": cap["points_per_s"], "lambda_req_per_s": first["lambda_req_per_s"],
+            "lambda_frac_of_capacity": first["lambda_frac_of_capacity"],
+            "points_per_s": first["points_per_s"], "p50_s": first["p50_s"], "p99_s": first["p99_s"],
+            "mean_queue_s": first["mean_queue_s"], "by_lambda": live,
             "single_request_fp64_points_per_s": single}
 
 
@@ -229,7 +245,8 @@ def side_path(F, mesh, Es, precision, B, device, rank, ws):
     """One warm-up and one timed step of another precision path."""
     import torch
     from paper_1104_0623_gb300.shard import step_energies
-    f = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=B, precision=precision)
+    f = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=B, precision=precision,
+                         energy_group=B)
     dev = f"cuda:{device}"
     st = torch.cuda.current_stream(device)
     E = [torch.tensor(step_energies(Es, k, rank, ws, B), dtype=torch.complex128, device=dev)
@@ -295,7 +312,8 @@ def main():
 
     mesh, Es = bench_mesh(args.mesh), W.c5_energies()
     B = args.batch
-    f = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=B, precision=args.path)
+    f = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=B, precision=args.path,
+                         energy_group=B)
     n, nb = mesh.n, f.n_bonds
     dev = f"cuda:{device}"
     E_dev = [torch.tensor(step_energies(Es, k, rank, ws, B), dtype=torch.complex128, device=dev)
@@ -370,7 +388,7 @@ def main():
            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD if args.mesh == "256x1024" else f"{args.mesh} profiling case",
-                      "energies_per_step": B, "leaf": 8, "path": args.path,
+                      "energies_per_step": B, "energy_groups_per_pass": 1, "leaf": 8, "path": args.path,
                       "l2": f"inputs larger than L2: {f.workspace_bytes(B) / 2**30:.1f} GiB "
                             f"resident U/R and scratch per step",
                       "parallelism": f"energy-sharded x{ws}, no data-path collective"},
@@ -384,6 +402,13 @@ def main():
         for other in ("fp64", "mixed", "mixed_ff"):
             if other != args.path:
                 paths[other] = side_path(F, mesh, Es, other, B, device, rank, ws)
+    # each path's whole-pass algorithmic rate against the FP64 peak (nominal, at
+    # the sampled clock) and against the probe-measured DMMA rate
+    for v in paths.values():
+        tf = f.stats.flops_lesser * v["value"] / 1e12
+        v["algorithmic_tflops"] = tf
+        v["frac_of_fp64_peak"] = tf / peak64
+        v["frac_of_measured_fp64_dmma"] = tf / FP64_DMMA_MEASURED_TFLOPS
     out["paths"] = paths
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.mesh == "256x1024":
         def gpu_solver(precision):
@@ -400,7 +425,9 @@ def main():
                 out["accuracy_vs_oracle"][other] = accuracy_at(acc["energy"], mesh, gpu_solver(other),
                                                                cpu_baseline.ref)
     if rank == 0 and ws == 1 and args.serve_requests > 0 and args.mesh == "256x1024":
-        out["serving"] = serving(device, args.serve_requests)
+        out["serving"] = serving(device, args.serve_requests,
+                                 "mixed" if args.path == "fp64" else args.path,
+                                 lam_fracs=[float(x) for x in args.serve_lambdas.split(",")])
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:

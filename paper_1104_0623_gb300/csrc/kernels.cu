@@ -335,6 +335,29 @@ __device__ __forceinline__ int pivot_row(const T* a, int ld, int k, int s, typen
   return *sh_p;
 }
 
+// row[j] = fms(f, rk[j], row[j]) for j = j0 + lane, j0 + lane + 32, ... < s
+// (row[skip] reads as zero).  Float-float keeps four loads in flight per lane
+// before the arithmetic (measured faster); FP64 loads one at a time (more
+// registers cost it occupancy).  Each entry sees exactly one fms either way.
+template <class X, class T>
+__device__ __forceinline__ void row_update(T* row, const T* rk, T f, int j0, int s, int lane,
+                                           int skip) {
+  constexpr int U = std::is_same<typename X::M, float>::value ? 4 : 1;
+  for (int jb = j0 + lane; jb < s; jb += 32 * U) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = jb + 32 * u;
+      if (j < s) v[u] = (j == skip) ? X::zero() : row[j];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = jb + 32 * u;
+      if (j < s) row[j] = X::fms(f, rk[j], v[u]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- inversion
 // Gauss-Jordan with partial pivoting, in place on the leading s x s block of
 // a (leading dimension ld); colk, rowk: s entries of scratch, piv: s ints.
@@ -378,12 +401,7 @@ __device__ void gauss_jordan(T* a, int ld, int s, T* colk, T* rowk, int* piv, in
     __syncthreads();
     for (int i = warp; i < s; i += nwarp) {
       if (i == k) continue;
-      const T f = colk[i];
-      T* row = a + (int64_t)i * ld;
-      for (int j = lane; j < s; j += 32) {
-        T v = (j == k) ? X::zero() : row[j];
-        row[j] = X::fms(f, rowk[j], v);
-      }
+      row_update<X>(a + (int64_t)i * ld, rowk, colk[i], 0, s, lane, k);
     }
     __syncthreads();
   }
@@ -530,8 +548,7 @@ __global__ void __launch_bounds__(kInvThreads) k_lu(const InvOp* __restrict__ op
     __syncthreads();
     for (int i = k + 1 + warp; i < s; i += nwarp) {
       T* row = a + (int64_t)i * ld;
-      const T l = row[k];
-      for (int j = k + 1 + lane; j < s; j += 32) row[j] = X::fms(l, rowk[j], row[j]);
+      row_update<X>(row, rowk, row[k], k + 1, s, lane, -1);
     }
     __syncthreads();
   }
@@ -743,7 +760,7 @@ struct TrsmArith<true> {
 };
 
 constexpr int kTrsmW = 8;        // columns per panel
-constexpr int kTrsmRowsMax = 16; // rows per CTA at most
+constexpr int kTrsmRowsMax = 16; // rows per CTA at most (24 measured slower)
 constexpr int kPanelThreads = kTrsmW * kTrsmRowsMax;  // 4 whole warps
 static_assert(kPanelThreads % 32 == 0 && 32 % kTrsmW == 0, "panel lanes must tile warps");
 
