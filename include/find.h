@@ -96,7 +96,10 @@ typedef struct {
   int gemm_small_max;       /* a Schur-update or leaf product whose larger
                                output side is at most this runs on 32x32
                                tiles, a larger one on 64x64 tiles (a tuning
-                               knob; results do not depend on it); 0 = 32      */
+                               knob; results do not depend on it); 0 = per
+                               product: 64x64 unless that pads more area than
+                               the 32x32 tiling, by more than 20 % for
+                               float-float and complex64, at all for FP64      */
 } find_desc;
 
 /* find_desc.flags.  With the closed-form leads A = A^T, so every U is complex

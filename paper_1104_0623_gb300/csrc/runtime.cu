@@ -163,10 +163,23 @@ int64_t leaf_slot_elems(const findgb::LeafOp& op, bool lesser) {
 }
 
 // Adds one GEMM op to a stage, assigning its tiles to the small or big class.
+// Tile class of a product.  small_max > 0: 32x32 tiles when the larger output
+// side is at most small_max.  small_max == 0 (default): 64x64 tiles unless
+// their padded area exceeds the 32x32 tiling's by more than a margin: 20 %
+// for float-float and complex64 (the big tile reloads and splits each operand
+// half as often and measured ~20 % more efficient per useful flop), none for
+// FP64 (both tiles keep the FP64 pipe nearly full, so padding decides).
+bool big_tiles(int m, int n, int small_max, Arith arith) {
+  if (small_max > 0) return std::max(m, n) > small_max;
+  const double p64 = 4096.0 * ((m + 63) / 64) * ((n + 63) / 64);
+  const double p32 = 1024.0 * ((m + 31) / 32) * ((n + 31) / 32);
+  return p64 <= (arith == kFP64 ? 1.0 : 1.2) * p32;
+}
+
 void add_gemm(findgb::GemmOp g, std::vector<findgb::GemmOp>& ops, std::vector<int>* maps,
               Stage* st, Arith arith, int small_max) {
   if (g.m == 0 || g.n == 0) return;
-  bool is_big = std::max(g.m, g.n) > small_max;
+  bool is_big = big_tiles(g.m, g.n, small_max, arith);
   const int cls = 2 * (int)arith + (is_big ? 1 : 0);
   st->fl[cls] += 8.0 * g.m * g.n * (double)(g.k + (g.A2 ? g.k2 : 0));
   int bm = is_big ? 64 : 32;
@@ -233,7 +246,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
   const bool ff_all = h->desc.precision == FIND_MIXED_FF;
   // shared-memory inversion only on request: measured slower than the
   // global-memory kernel (one 200 KB CTA per SM cannot hide its barriers)
-  const int small_max = h->desc.gemm_small_max > 0 ? h->desc.gemm_small_max : 32;
+  const int small_max = h->desc.gemm_small_max;  // 0: chosen per product by padding
   const int inv_smem = h->desc.invert_smem <= 0 ? 0
                        : std::min(h->desc.invert_smem, findgb::invert_smem_max());
   const int top_levels = h->desc.fp64_top_levels < 0 ? 2 : h->desc.fp64_top_levels;

@@ -9,7 +9,8 @@ the results independent of it):
                       small, launch-bound problems shrinks);
 * ``energy_group``    energies per concurrent stream group within a pass;
 * ``gemm_small_max``  output size up to which a GEMM runs on 32x32 tiles
-                      rather than 64x64 (tile shape per product);
+                      rather than 64x64 (tile shape per product; 0 = by
+                      padding area, 4096 = all on 32x32);
 * ``invert_smem``     bordered leaf systems up to this size are inverted in
                       shared memory.
 
@@ -30,9 +31,9 @@ import time
 
 import numpy as np
 
-DEFAULTS = {"leaf": 8, "energy_group": 8, "gemm_small_max": 32, "invert_smem": 0}
+DEFAULTS = {"leaf": 8, "energy_group": 8, "gemm_small_max": 0, "invert_smem": 0}
 SPACE = [("leaf", (6, 8, 10, 12)),
-         ("gemm_small_max", (16, 32, 48)),
+         ("gemm_small_max", (32, 64, 4096)),  # 0 (default): by padding; 4096: all 32x32
          ("energy_group", (4, 8, 16, 32)),
          ("invert_smem", (0, 112))]
 

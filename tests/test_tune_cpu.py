@@ -11,8 +11,9 @@ from paper_1104_0623_gb300 import tune
 
 
 def fake_cost(params):
-    # best at leaf 10, tiles 48, group 16, no shared-memory inversion
-    return (abs(params["leaf"] - 10) + abs(params["gemm_small_max"] - 48) / 16
+    # best at leaf 10, 64x64 tiles above 64, group 16, no shared-memory inversion
+    tiles = abs(np.log2(params["gemm_small_max"]) - 6) if params["gemm_small_max"] else 3.0
+    return (abs(params["leaf"] - 10) + tiles
             + abs(np.log2(params["energy_group"]) - 4) + params["invert_smem"] / 112 + 1.0)
 
 
@@ -33,7 +34,7 @@ def test_coordinate_descent_finds_the_best_knobs_and_caches_them(tmp_path, monke
     mesh = W.c3()[0]
     E = W.c3_energies()
     best = t.tune(mesh, E, "mixed_ff", 16)
-    assert best == {"leaf": 10, "gemm_small_max": 48, "energy_group": 16, "invert_smem": 0}
+    assert best == {"leaf": 10, "gemm_small_max": 64, "energy_group": 16, "invert_smem": 0}
     # every candidate is timed once; the default first
     assert calls[0] == tune.DEFAULTS
     assert len(calls) == len({tuple(sorted(c.items())) for c in calls})
