@@ -555,6 +555,98 @@ __global__ void __launch_bounds__(kInvThreads) k_lu(const InvOp* __restrict__ op
   from_work<X>(g, ld, s);
 }
 
+// Float-float LU, blocked by panels of PW columns: each panel is factorised
+// column by column (pivot search, full-row interchange, scaling, update of the
+// panel's own later columns); then its U rows are completed over the trailing
+// columns (kept in shared memory) and the trailing block takes one rank-PW
+// update.  Every entry sees the same operations in the same order as in
+// k_lu, so the factors are identical; the trailing block, which at large s
+// does not fit in L2, crosses HBM once per panel instead of once per column.
+constexpr int kLuPanel = 4;
+
+template <int PW>
+__global__ void __launch_bounds__(kInvThreads, 2) k_lu_panel(const InvOp* __restrict__ ops,
+                                                            int* __restrict__ status, int e_base,
+                                                            int e_off) {
+  typedef GA<true> X;
+  typedef X::T T;
+  const InvOp op = ops[blockIdx.x];
+  const int e = blockIdx.y + e_off;
+  const int s = op.s, ld = op.ld;
+  if (s == 0) return;
+  cplx* g = op.M + (int64_t)e * op.estride;
+  int* piv = op.piv + (int64_t)e * op.piv_estride;
+  extern __shared__ double2 lu_smem[];
+  T* urow = reinterpret_cast<T*>(lu_smem);  // PW x s: the panel's U rows
+  __shared__ X::M red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int sh_p;
+  __shared__ T sh_pinv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int nt = blockDim.x;
+  to_work<X>(g, ld, s);
+  T* a = reinterpret_cast<T*>(g);
+  for (int k0 = 0; k0 < s; k0 += PW) {
+    const int w = min(PW, s - k0), k1 = k0 + w;
+    for (int k = k0; k < k1; ++k) {
+      const int p = pivot_row<X>(a, ld, k, s, red_v, red_i, &sh_p);
+      if (tid == 0) piv[k] = p;
+      if (p != k)
+        for (int j = tid; j < s; j += nt) {
+          T t0 = a[(int64_t)k * ld + j];
+          a[(int64_t)k * ld + j] = a[(int64_t)p * ld + j];
+          a[(int64_t)p * ld + j] = t0;
+        }
+      __syncthreads();
+      if (tid == 0) {  // the pivot reciprocal, once per step, in FP64 (Smith)
+        const T pv = a[(int64_t)k * ld + k];
+        cplx pinv = cmk(0, 0);
+        if (X::is_zero(pv)) atomicMin(status, e_base + e);
+        else pinv = crecip(X::to(pv));
+        sh_pinv = X::from(pinv);
+      }
+      __syncthreads();
+      const T pinv = sh_pinv;
+      for (int i = k + 1 + tid; i < s; i += nt) {
+        // scale the column, then update the rest of this row inside the panel
+        T* row = a + (int64_t)i * ld;
+        const T l = X::scale(row[k], pinv);
+        row[k] = l;
+        for (int c = k + 1; c < k1; ++c) row[c] = X::fms(l, a[(int64_t)k * ld + c], row[c]);
+      }
+      __syncthreads();
+    }
+    // the panel's U rows over the trailing columns, one column per thread
+    for (int j = k1 + tid; j < s; j += nt) {
+      for (int t = 0; t < w; ++t) {
+        T u = a[(int64_t)(k0 + t) * ld + j];
+        for (int t2 = 0; t2 < t; ++t2)
+          u = X::fms(a[(int64_t)(k0 + t) * ld + k0 + t2], urow[t2 * s + j], u);
+        urow[t * s + j] = u;
+        a[(int64_t)(k0 + t) * ld + j] = u;
+      }
+    }
+    __syncthreads();
+    // the trailing block: one rank-w update, a warp per row
+    for (int i = k1 + warp; i < s; i += nwarp) {
+      T* row = a + (int64_t)i * ld;
+      T l[PW];
+#pragma unroll
+      for (int t = 0; t < PW; ++t)
+        if (t < w) l[t] = row[k0 + t];
+      for (int j = k1 + lane; j < s; j += 32) {
+        T v = row[j];
+#pragma unroll
+        for (int t = 0; t < PW; ++t)
+          if (t < w) v = X::fms(l[t], urow[t * s + j], v);
+        row[j] = v;
+      }
+    }
+    __syncthreads();
+  }
+  from_work<X>(g, ld, s);
+}
+
 // ---------------------------------------------------------------- grouped complex GEMM
 // Operands are complex128 in memory; CT is the arithmetic type: double2 (FP64
 // path) or float2 (complex64 arithmetic of the mixed path, operands rounded
@@ -963,14 +1055,23 @@ void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_bas
   }
 }
 
-void launch_lu(const InvOp* ops, int nops, int* status, int e_base, int nE, cudaStream_t st,
-               int e_off, int df) {
-  if (nops == 0) return;
+void launch_lu(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
+               cudaStream_t st, int e_off, int df) {
+  if (nops == 0 || max_s <= 0) return;
   dim3 grid(nops, nE);
-  if (df)
-    k_lu<true><<<grid, kInvThreads, kMaxInvert * sizeof(cplx), st>>>(ops, status, e_base, e_off);
-  else
+  if (df) {
+    // PW rows of the largest s of the launch (s <= kMaxInvert)
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(k_lu_panel<kLuPanel>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kLuPanel * kMaxInvert * (int)sizeof(float4));
+      attr_set = true;
+    }
+    const size_t smem = (size_t)kLuPanel * max_s * sizeof(float4);
+    k_lu_panel<kLuPanel><<<grid, kInvThreads, smem, st>>>(ops, status, e_base, e_off);
+  } else {
     k_lu<false><<<grid, kInvThreads, kMaxInvert * sizeof(cplx), st>>>(ops, status, e_base, e_off);
+  }
 }
 
 int invert_smem_max() { return kInvSmemMax; }

@@ -101,8 +101,8 @@ void launch_assemble(const AsmOp* ops, const int* row_op, int nrows, const Pos* 
 void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
                    cudaStream_t st, int e_off = 0, int df = 0, int in_smem = 0);
 int invert_smem_max();
-void launch_lu(const InvOp* ops, int nops, int* status, int e_base, int nE, cudaStream_t st,
-               int e_off = 0, int df = 0);
+void launch_lu(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
+               cudaStream_t st, int e_off = 0, int df = 0);
 // df = 1: the row block is carried in float-float arithmetic
 void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int max_s, int nE,
                  cudaStream_t st, int df = 0, int e_off = 0);

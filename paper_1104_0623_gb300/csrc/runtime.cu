@@ -723,7 +723,8 @@ void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, boo
     for (int c = 0; c < 2; ++c)
       if (lv.ninv[c] > 0)
         timed(h, st, c ? 13 : 3, lv.fl_inv[c] * nb, 0.0, [&] {
-          findgb::launch_lu(at<findgb::InvOp>(h, lv.inv[c]), lv.ninv[c], status, e_base, nb, st, e_off, c);
+          findgb::launch_lu(at<findgb::InvOp>(h, lv.inv[c]), lv.ninv[c], lv.inv_max[c], status, e_base,
+                            nb, st, e_off, c);
         });
     for (int c = 0; c < 2; ++c)
       if (lv.ntrsm[c] > 0)
@@ -955,8 +956,8 @@ void run_level_static(find_handle* h, const StaticView& sv, const Level& lv,
                             lv.inv_max[c], status, e_base, nb, st, 0, c & 1, c >> 1);
   } else {
     for (int c = 0; c < 2; ++c)
-      findgb::launch_lu(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv[c])), lv.ninv[c], status,
-                        e_base, nb, st, 0, c);
+      findgb::launch_lu(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv[c])), lv.ninv[c],
+                        lv.inv_max[c], status, e_base, nb, st, 0, c);
     for (int c = 0; c < 2; ++c)
       findgb::launch_trsm(reinterpret_cast<const findgb::TrsmOp*>(meta(lv.trsm)),
                           reinterpret_cast<const int*>(meta(lv.trsm_map[c])), lv.ntrsm[c], lv.rb,
