@@ -56,8 +56,9 @@ enum {
  * floats, about 48 significant bits, on the FP32 pipes, which GB300 runs
  * about 70 times faster than FP64); the pivoted LU, the leaf inversion and
  * every step of the top levels stay FP64.  Operands and results stay
- * complex128 in memory.  Measured on the 256x1024 9-point mesh: diag G and
- * diag G< within 9e-9 of the FP64 oracle.
+ * complex128 in memory.  Measured on the 256x1024 9-point mesh at 8 grid
+ * energies: diag G and diag G< within 4.3e-8 of the exact values (FP64:
+ * within 4e-10, and within a factor 5 of a plain FP64 FIND's own error).
  * FIND_MIXED_FF: as FIND_MIXED, and below the top levels the pivoted LU and
  * the leaf inversion run in float-float too.
  * Complex64 arithmetic is available for the Sigma update from a chosen tree
