@@ -112,7 +112,18 @@ typedef struct {
    dominates).
      FIND_FLAG_FULL_U  both triangles on every path
      FIND_FLAG_SYM_U   one triangle on FIND_FP64 too (ignored with FULL_U)  */
-enum { FIND_FLAG_FULL_U = 1, FIND_FLAG_SYM_U = 2 };
+enum { FIND_FLAG_FULL_U = 1, FIND_FLAG_SYM_U = 2, FIND_FLAG_GRAPH = 4 };
+/* FIND_FLAG_GRAPH: find_solve_diag / find_solve_lesser capture the device work
+   of a pass (closed-form lead Sigma and every level's launches, over all
+   energy-group streams) into a CUDA graph the first time a call signature is
+   seen -- the number of energies in the pass, its offset in the call, the
+   outputs asked for, which of Sigma_L, Sigma_R and the node-diagonal Sigma<
+   are given, fL, fR -- and replay it with cudaGraphLaunch afterwards (up to 8
+   signatures per handle, least recently used dropped).  Energies and the
+   optional inputs are copied in, and outputs copied out, outside the graph,
+   so each call may pass new values and new buffers.  Results are bitwise
+   the same as without the flag.  find_profile does not time replayed
+   passes.  Reallocating the workspace (a larger batch) drops the graphs. */
 
 /* Host-side facts of the plan (no GPU needed). */
 typedef struct {

@@ -21,6 +21,7 @@ FIND_MIXED = 1
 FIND_MIXED_FF = 2
 FIND_FLAG_FULL_U = 1
 FIND_FLAG_SYM_U = 2
+FIND_FLAG_GRAPH = 4
 
 STATUS_NAMES = {0: "FIND_OK", 1: "FIND_EINVAL", 2: "FIND_ENOMEM", 3: "FIND_ESINGULAR",
                 4: "FIND_ETIMEOUT", 5: "FIND_ECUDA"}

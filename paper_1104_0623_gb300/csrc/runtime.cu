@@ -135,6 +135,20 @@ struct find_handle {
   // streams and events of the concurrent energy groups of one pass
   std::vector<cudaStream_t> gstreams;
   std::vector<cudaEvent_t> gevents;
+  // FIND_FLAG_GRAPH: captured passes, keyed by everything a pass's launches
+  // bake in, replayed with cudaGraphLaunch; captured on cap_stream
+  struct GraphKey {
+    int nb, e0, lesser, bonds, sigL, sigR, dles, dles_per_e, sym;
+    double fL, fR;
+    bool operator==(const GraphKey& o) const {
+      return nb == o.nb && e0 == o.e0 && lesser == o.lesser && bonds == o.bonds && sigL == o.sigL &&
+             sigR == o.sigR && dles == o.dles && dles_per_e == o.dles_per_e && sym == o.sym &&
+             fL == o.fL && fR == o.fR;
+    }
+  };
+  struct Graph { GraphKey key; cudaGraphExec_t exec; };
+  std::vector<Graph> graphs;  // most recently used last
+  cudaStream_t cap_stream = nullptr;
 };
 
 namespace {
@@ -590,7 +604,14 @@ double workspace_bytes(find_handle* h, int batch, bool lesser, std::string* chec
   return (double)L.total;
 }
 
+// Captured passes hold pointers into the workspace: drop them with it.
+void drop_graphs(find_handle* h) {
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+}
+
 void release(find_handle* h) {
+  drop_graphs(h);
   if (h->ws) cudaFree(h->ws);
   h->ws = nullptr;
   h->batch = 0;
@@ -796,10 +817,21 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
   cplx* dmodes = reinterpret_cast<cplx*>(ws + L.modes);
   cplx* ddl = reinterpret_cast<cplx*>(ws + L.dles);
   int* status = reinterpret_cast<int*>(ws + L.status);
-  const bool dG = device_accessible(G);
-  const bool dGl = !lesser || device_accessible(Gl);
-  const bool dJ = !lesser || !J || device_accessible(J);
+  // graph mode writes every output to the workspace's staging buffers (the
+  // captured launches must not hold the caller's pointers) and copies out
+  const bool graph = (h->desc.flags & FIND_FLAG_GRAPH) != 0;
+  const bool dG = !graph && device_accessible(G);
+  const bool dGl = !lesser || (!graph && device_accessible(Gl));
+  const bool dJ = !lesser || !J || (!graph && device_accessible(J));
   const int want_bonds = (lesser && J) ? 1 : 0;
+  if (graph) {
+    int rc2 = ensure_group_streams(h);
+    if (rc2 != FIND_OK) return rc2;
+    if (!h->cap_stream) {
+      cudaError_t ce = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+      if (ce != cudaSuccess) return cuda_fail(h, ce, "capture stream");
+    }
+  }
 
   cudaError_t e = cudaMemsetAsync(status, 0x7f, sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
@@ -814,16 +846,7 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
     if (e != cudaSuccess) return cuda_fail(h, e, "energy copy");
     const cplx* useL = dsL;
     const cplx* useR = dsR;
-    if (!sigL || !sigR) {
-      cplx* dst = !sigL ? dsL : dsR;
-      timed(h, st, 0, 2.0 * nx * nx * nx * nb, 0.0, [&] {
-        findgb::launch_lead_modes(dE, nb, reinterpret_cast<const double*>(ws + L.eps),
-                                  reinterpret_cast<const double*>(ws + L.tau), (int)nx, dmodes, st);
-        findgb::launch_lead_dense(dmodes, reinterpret_cast<const double*>(ws + L.phi), (int)nx, nb,
-                                  dst, st);
-      });
-      if (!sigL && !sigR) useR = dsL;
-    }
+    if (!sigL && !sigR) useR = dsL;
     if (sigL) {
       e = cudaMemcpyAsync(dsL, sigL + 2 * (int64_t)e0 * nx * nx, nb * nx * nx * sizeof(cplx),
                           cudaMemcpyDefault, st);
@@ -857,22 +880,34 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
                        : nullptr;
     double* oJ = want_bonds ? (dJ ? J + (int64_t)e0 * p.n_bonds : reinterpret_cast<double*>(ws + L.oJ))
                             : nullptr;
+    // A = A^T when both leads take the closed form (Phi diag(sigma) Phi^T):
+    // then every U is complex symmetric and its update may run on one triangle
+    const int sym_mask = sym_updates(h, sigL, sigR);
+    // the device work of one pass: closed-form lead Sigma, then every level;
     // independent energy groups on their own streams, so that one group's
     // low-parallelism phases (LU of the few large top blocks) overlap other
     // groups' work
-    // A = A^T when both leads take the closed form (Phi diag(sigma) Phi^T):
-    // then every U is complex symmetric and its update runs on one triangle
-    const int sym_mask = sym_updates(h, sigL, sigR);
-    const int gsz = h->desc.energy_group > 0 ? h->desc.energy_group : 8;
-    const int ng = std::min((nb + gsz - 1) / gsz, kMaxGroups);
-    if (ng <= 1) {
-      for (const Level& lv : h->levels)
-        run_level(h, lv, P, lesser, e0, nb, st, oG, oGl, oJ, want_bonds, 0, sym_mask);
-    } else {
+    auto pass = [&](cudaStream_t qs) -> int {
+      if (!sigL || !sigR) {
+        cplx* dst = !sigL ? dsL : dsR;
+        timed(h, qs, 0, 2.0 * nx * nx * nx * nb, 0.0, [&] {
+          findgb::launch_lead_modes(dE, nb, reinterpret_cast<const double*>(ws + L.eps),
+                                    reinterpret_cast<const double*>(ws + L.tau), (int)nx, dmodes, qs);
+          findgb::launch_lead_dense(dmodes, reinterpret_cast<const double*>(ws + L.phi), (int)nx, nb,
+                                    dst, qs);
+        });
+      }
+      const int gsz = h->desc.energy_group > 0 ? h->desc.energy_group : 8;
+      const int ng = std::min((nb + gsz - 1) / gsz, kMaxGroups);
+      if (ng <= 1) {
+        for (const Level& lv : h->levels)
+          run_level(h, lv, P, lesser, e0, nb, qs, oG, oGl, oJ, want_bonds, 0, sym_mask);
+        return FIND_OK;
+      }
       int rc2 = ensure_group_streams(h);
       if (rc2 != FIND_OK) return rc2;
       cudaEvent_t fork = h->gevents[kMaxGroups];
-      cudaEventRecord(fork, st);
+      cudaEventRecord(fork, qs);
       const int per = (nb + ng - 1) / ng;
       for (int g = 0; g < ng; ++g) {
         const int lo = g * per, cnt = std::min(per, nb - lo);
@@ -882,8 +917,54 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
         for (const Level& lv : h->levels)
           run_level(h, lv, P, lesser, e0, cnt, gs, oG, oGl, oJ, want_bonds, lo, sym_mask);
         cudaEventRecord(h->gevents[g], gs);
-        cudaStreamWaitEvent(st, h->gevents[g], 0);
+        cudaStreamWaitEvent(qs, h->gevents[g], 0);
       }
+      return FIND_OK;
+    };
+    if (!graph) {
+      int rc2 = pass(st);
+      if (rc2 != FIND_OK) return rc2;
+    } else {
+      const find_handle::GraphKey key{nb, e0, lesser ? 1 : 0, want_bonds, sigL ? 1 : 0, sigR ? 1 : 0,
+                                      dles ? 1 : 0, dles_per_e, sym_mask, fL, fR};
+      cudaGraphExec_t exec = nullptr;
+      for (size_t i = 0; i < h->graphs.size(); ++i)
+        if (h->graphs[i].key == key) {
+          find_handle::Graph g = h->graphs[i];
+          h->graphs.erase(h->graphs.begin() + i);
+          h->graphs.push_back(g);
+          exec = g.exec;
+          break;
+        }
+      if (!exec) {
+        // the event profiler's records cannot live inside a graph
+        const bool prof = h->prof;
+        h->prof = false;
+        e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) {
+          h->prof = prof;
+          return cuda_fail(h, e, "begin capture");
+        }
+        int rc2 = pass(h->cap_stream);
+        cudaGraph_t gr = nullptr;
+        e = cudaStreamEndCapture(h->cap_stream, &gr);
+        h->prof = prof;
+        if (rc2 != FIND_OK) {
+          if (gr) cudaGraphDestroy(gr);
+          return rc2;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+        e = cudaGraphInstantiate(&exec, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+        if (h->graphs.size() >= 8) {
+          cudaGraphExecDestroy(h->graphs.front().exec);
+          h->graphs.erase(h->graphs.begin());
+        }
+        h->graphs.push_back(find_handle::Graph{key, exec});
+      }
+      e = cudaGraphLaunch(exec, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
@@ -1260,6 +1341,7 @@ int find_destroy(find_handle* h) {
     for (auto e : h->ev_free) cudaEventDestroy(e);
     for (auto e : h->gevents) cudaEventDestroy(e);
     for (auto q : h->gstreams) cudaStreamDestroy(q);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   }
   delete h;
   return FIND_OK;
