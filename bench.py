@@ -54,6 +54,25 @@ FF_INST_PER_CMAC = 54
 DOMINANT_TRAFFIC = {}
 
 
+def measured_hbm_gbs():
+    """The HBM copy bandwidth of MEASURED_PEAKS.json (GB/s), or None."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+        v = d.get(k)
+        if isinstance(v, (int, float)):
+            return float(v)
+        if isinstance(v, dict):
+            for kk in ("value", "gbs", "burst"):
+                if isinstance(v.get(kk), (int, float)):
+                    return float(v[kk])
+    return None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,6 +403,15 @@ def main():
                     "paths most of them run in float-float or complex64, so frac can exceed 1"}
     kernels = {p["name"]: {"launches": p["launches"], "ms": round(p["ms"], 3),
                            "share": p["ms"] / sum(q["ms"] for q in prof)} for p in prof if p["launches"]}
+    # the HBM-bound kernels (gather of M and Sigma_M, extraction of the
+    # outputs): algorithmic bytes moved / time, against the measured copy peak
+    hbm_peak = measured_hbm_gbs()
+    for p in prof:
+        if p["launches"] and p["bytes"] > 0 and p["ms"] > 0:
+            gbs = p["bytes"] / (p["ms"] / 1e3) / 1e9
+            kernels[p["name"]]["achieved_gbs"] = gbs
+            if hbm_peak:
+                kernels[p["name"]]["frac_of_measured_hbm"] = gbs / hbm_peak
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

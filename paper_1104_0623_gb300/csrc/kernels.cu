@@ -697,7 +697,9 @@ struct Cx<float4> {
 // Tile BM x BN per CTA, BK deep; each thread owns a 4 x 4 block of outputs at
 // rows ty + i*BM/4, cols tx + j*BN/4.  alpha is folded into the A tile.
 template <int BM, int BN, int BK, class CT>
-__global__ void __launch_bounds__((BM / 4) * (BN / 4), (sizeof(CT) == 16 && BM == 64) ? 2 : 1)
+// float-float: at most 128 registers, so 16 warps share an SM (2 CTAs of the
+// 64x64 tile, 8 of the 32x32 one)
+__global__ void __launch_bounds__((BM / 4) * (BN / 4), sizeof(CT) == 16 ? (BM == 64 ? 2 : 8) : 1)
     k_zgemm(const GemmOp* __restrict__ ops,
                                                                const int* __restrict__ tile_op,
                                                                int e_off, int sym_mask) {

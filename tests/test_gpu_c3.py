@@ -47,6 +47,10 @@ def test_c3_ragged_batch_autotuned(F, tmp_path):
     backend = serve.GpuBackend(precision="mixed_ff", chunk=16, tuner=tuner)
     mixed = serve.solve_ragged([(m, Es) for m in meshes], backend, slots=4, chunk=16)
     assert len(tuner.cache) == len(meshes)
+    for key, entry in tuner.log:
+        print(f"tuned {key.split(':')[0]}: {entry['params']} "
+              f"{1e3 * entry['seconds_per_energy']:.2f} ms/E (defaults "
+              f"{1e3 * entry['default_seconds_per_energy']:.2f}), {entry['candidates']} candidates")
     for k, mesh in enumerate(meshes):
         params = tuner.tune(mesh, Es[:16], "mixed_ff", 16)
         f = F.Find.from_mesh(mesh, max_batch=32, precision="fp64")
