@@ -644,7 +644,8 @@ __global__ void __launch_bounds__(kInvThreads, 2) k_lu_panel(const InvOp* __rest
     }
     __syncthreads();
   }
-  from_work<X>(g, ld, s);
+  // the factors stay float-float words: their only reader, the float-float
+  // TRSM, takes them as they are (k_trsm<true, true>)
 }
 
 // ---------------------------------------------------------------- grouped complex GEMM
@@ -858,12 +859,27 @@ constexpr int kTrsmRowsMax = 16; // rows per CTA at most (24 measured slower)
 constexpr int kPanelThreads = kTrsmW * kTrsmRowsMax;  // 4 whole warps
 static_assert(kPanelThreads % 32 == 0 && 32 % kTrsmW == 0, "panel lanes must tile warps");
 
+// Entries of the LU factors of M(S,S).  FF: the float-float LU left them as
+// float-float words (re.hi, re.lo, im.hi, im.lo) in the 16 bytes of each
+// complex128 slot, so they are read as they are; otherwise they are
+// complex128 and split on reading.
+template <class X, bool FF>
+__device__ __forceinline__ typename X::T fac_in(const cplx* p) {
+  if constexpr (FF) return *reinterpret_cast<const float4*>(p);
+  else return X::in(*p);
+}
+template <bool FF>
+__device__ __forceinline__ cplx fac_wide(const cplx* p) {
+  if constexpr (FF) return df_wide(*reinterpret_cast<const float4*>(p));
+  else return *p;
+}
+
 // Y(r, i) -= sum_{t < w} Y(r, j0 + t) * F(j0 + t, i) for rows r < rows and
 // columns i in [c0, c1), F the factor in a (leading dimension ld).  Threads
 // take (column, row group) pairs so that narrow updates still occupy the
 // block; each element sees the same operations in the same order as one
 // thread per column would give it.
-template <class X, class T>
+template <class X, bool FF, class T>
 __device__ __forceinline__ void rank_update(T* Y, const cplx* a, int ld, int s, int rows, int j0,
                                             int w, int c0, int c1, int tid, int nt) {
   constexpr int W = kTrsmW;
@@ -876,7 +892,7 @@ __device__ __forceinline__ void rank_update(T* Y, const cplx* a, int ld, int s, 
     T u[W];
 #pragma unroll
     for (int t = 0; t < W; ++t)
-      if (t < w) u[t] = X::in(a[(int64_t)(j0 + t) * ld + i]);
+      if (t < w) u[t] = fac_in<X, FF>(a + (int64_t)(j0 + t) * ld + i);
     const int r1 = min(rows, (rg + 1) * rpt);
     for (int r = rg * rpt; r < r1; ++r) {
       T v = Y[r * s + i];
@@ -888,7 +904,7 @@ __device__ __forceinline__ void rank_update(T* Y, const cplx* a, int ld, int s, 
   }
 }
 
-template <bool DF>
+template <bool DF, bool FF>
 __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
                                               const int* __restrict__ tile_op, int rb, int e_off) {
   typedef TrsmArith<DF> X;
@@ -917,12 +933,13 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
     const int w = min(W, s - j0);
     for (int idx = tid; idx < w * w; idx += nt) {
       const int t = idx / w, t2 = idx % w;
-      const cplx u = a[(int64_t)(j0 + t) * ld + j0 + t2];
+      const cplx* up = a + (int64_t)(j0 + t) * ld + j0 + t2;
       if (t == t2) {
+        const cplx u = fac_wide<FF>(up);
         const bool z = (u.x == 0.0 && u.y == 0.0);  // zero only if the LU flagged it
         dgl[t] = X::in(z ? cmk(0, 0) : crecip(u));
       } else {
-        pan[t][t2] = X::in(u);
+        pan[t][t2] = fac_in<X, FF>(up);
       }
     }
     __syncthreads();
@@ -938,7 +955,7 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
       if (act) Y[r * s + j0 + c] = yv;
     }
     __syncthreads();
-    rank_update<X>(Y, a, ld, s, rows, j0, w, j0 + w, s, tid, nt);  // the later columns
+    rank_update<X, FF>(Y, a, ld, s, rows, j0, w, j0 + w, s, tid, nt);  // the later columns
     __syncthreads();
   }
   // backward: Z L = Y with L unit lower, panels of W columns right to left
@@ -946,7 +963,7 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
     const int j0 = max(0, je - W), w = je - j0;
     for (int idx = tid; idx < w * w; idx += nt) {
       const int t = idx / w, t2 = idx % w;
-      if (t2 < t) pan[t][t2] = X::in(a[(int64_t)(j0 + t) * ld + j0 + t2]);
+      if (t2 < t) pan[t][t2] = fac_in<X, FF>(a + (int64_t)(j0 + t) * ld + j0 + t2);
     }
     __syncthreads();
     if (tid < kPanelThreads) {
@@ -960,7 +977,7 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
       if (act) Y[r * s + j0 + c] = yv;
     }
     __syncthreads();
-    rank_update<X>(Y, a, ld, s, rows, j0, w, 0, j0, tid, nt);  // the earlier columns
+    rank_update<X, FF>(Y, a, ld, s, rows, j0, w, 0, j0, tid, nt);  // the earlier columns
     __syncthreads();
   }
   // L = Z P: column j of the result is column perm[j] of Z
@@ -1087,20 +1104,23 @@ int trsm_rows_per_block(int max_s) {
 }
 
 void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int max_s, int nE,
-                 cudaStream_t st, int df, int e_off) {
+                 cudaStream_t st, int df, int e_off, int ff_factors) {
   if (ntiles == 0 || max_s == 0) return;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_trsm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
-    cudaFuncSetAttribute(k_trsm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
+    cudaFuncSetAttribute(k_trsm<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
+    cudaFuncSetAttribute(k_trsm<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
+    cudaFuncSetAttribute(k_trsm<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
     attr_set = true;
   }
   size_t smem = (size_t)rb * max_s * sizeof(cplx) + (size_t)max_s * sizeof(int);
   dim3 grid(ntiles, nE);
-  if (df)
-    k_trsm<true><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
+  if (df && ff_factors)
+    k_trsm<true, true><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
+  else if (df)
+    k_trsm<true, false><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
   else
-    k_trsm<false><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
+    k_trsm<false, false><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
 }
 
 void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,

@@ -103,9 +103,11 @@ void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_bas
 int invert_smem_max();
 void launch_lu(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
                cudaStream_t st, int e_off = 0, int df = 0);
-// df = 1: the row block is carried in float-float arithmetic
+// df = 1: the row block is carried in float-float arithmetic; ff_factors = 1:
+// the LU factors of M(S,S) are float-float words (the float-float LU leaves
+// them so), else complex128
 void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int max_s, int nE,
-                 cudaStream_t st, int df = 0, int e_off = 0);
+                 cudaStream_t st, int df = 0, int e_off = 0, int ff_factors = 0);
 int trsm_rows_per_block(int max_s);
 // fp32 = 1: complex64 arithmetic on complex128 operands (mixed path);
 // fp32 = 2: float-float arithmetic (about 48 significant bits)

@@ -690,6 +690,13 @@ const char* kClassNames[kClasses] = {"lead",    "assemble", "invert",   "lu",   
 // profiler class of each GEMM launch class 2 * arith + big
 const int kGemmClass[6] = {5, 6, 8, 9, 10, 11};
 
+// 1 when the TRSM launch of class c (1: float-float) reads factors that the
+// float-float LU left as float-float words: on FIND_MIXED_FF the LU and the
+// TRSM of a level share their class; on FIND_MIXED the LU is always FP64.
+int ff_factors(const find_handle* h, int c) {
+  return (c == 1 && h->desc.precision == FIND_MIXED_FF) ? 1 : 0;
+}
+
 // 1 when every U update runs on one triangle (closed-form leads make
 // A = A^T): by default on the mixed paths only, see FIND_FLAG_SYM_U.
 int sym_updates(const find_handle* h, const void* sigL, const void* sigR) {
@@ -751,7 +758,7 @@ void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, boo
       if (lv.ntrsm[c] > 0)
         timed(h, st, c ? 12 : 4, lv.fl_trsm[c] * nb, 0.0, [&] {
           findgb::launch_trsm(at<findgb::TrsmOp>(h, lv.trsm), at<int>(h, lv.trsm_map[c]), lv.ntrsm[c],
-                              lv.rb, lv.max_s, nb, st, c, e_off);
+                              lv.rb, lv.max_s, nb, st, c, e_off, ff_factors(h, c));
         });
   }
   for (int k = 0; k < lv.nstages; ++k) {
@@ -1042,7 +1049,7 @@ void run_level_static(find_handle* h, const StaticView& sv, const Level& lv,
     for (int c = 0; c < 2; ++c)
       findgb::launch_trsm(reinterpret_cast<const findgb::TrsmOp*>(meta(lv.trsm)),
                           reinterpret_cast<const int*>(meta(lv.trsm_map[c])), lv.ntrsm[c], lv.rb,
-                          lv.max_s, nb, st, c);
+                          lv.max_s, nb, st, c, 0, ff_factors(h, c));
   }
   for (int k = 0; k < lv.nstages; ++k) {
     const Stage& s = lv.st[k];
