@@ -1206,6 +1206,10 @@ int find_create(const find_desc* d, find_handle** out) {
   if (d->stencil != 5 && d->stencil != 9) return fail(nullptr, FIND_EINVAL, "stencil must be 5 or 9");
   if (d->max_batch < 0) return fail(nullptr, FIND_EINVAL, "max_batch < 0");
   if (d->gemm_small_max < 0) return fail(nullptr, FIND_EINVAL, "gemm_small_max < 0");
+  if (d->flags & ~(FIND_FLAG_FULL_U | FIND_FLAG_SYM_U | FIND_FLAG_GRAPH))
+    return fail(nullptr, FIND_EINVAL, "unknown bit in flags");
+  if (d->energy_group < 0 || d->sigma_c64_depth < 0)
+    return fail(nullptr, FIND_EINVAL, "energy_group and sigma_c64_depth must be >= 0");
   find_handle* h = new (std::nothrow) find_handle();
   if (!h) return fail(nullptr, FIND_ENOMEM, "host allocation");
   h->desc = *d;

@@ -42,6 +42,8 @@ def test_library_exports_every_declared_symbol(F):
 
 @pytest.mark.parametrize("kw,msg", [
     (dict(nx=0, ny=4), "nx"), (dict(nx=4, ny=1), "ny"), (dict(nx=4, ny=4, stencil=7), "stencil"),
+    (dict(max_batch=-1), "max_batch"), (dict(gemm_small_max=-2), "gemm_small_max"),
+    (dict(energy_group=-1), "energy_group"), (dict(sigma_c64_depth=-1), "sigma_c64_depth"),
 ])
 def test_create_rejects_bad_arguments(F, kw, msg):
     args = dict(nx=4, ny=4, stencil=5)
@@ -49,6 +51,16 @@ def test_create_rejects_bad_arguments(F, kw, msg):
     with pytest.raises(F.FindError) as ei:
         F.Find(**args)
     assert ei.value.code == 1 and msg in str(ei.value)
+
+
+def test_create_rejects_unknown_flags(F):
+    import ctypes
+    d = F._abi.find_desc(4, 4, 5, 1.0, 0.0, None, 4.0, 8, F.FIND_FP64, 0, 0, 2, 0, 0, 0, 8, 0)
+    h = ctypes.c_void_p()
+    rc = F._abi.load().find_create(ctypes.byref(d), ctypes.byref(h))
+    assert rc == 1 and "flags" in F.find_last_error(None)
+    ok = F.Find(4, 4, full_u=True, sym_u=True, graph=True)  # every known bit
+    ok.close()
 
 
 def test_solve_rejects_null_outputs(F):
