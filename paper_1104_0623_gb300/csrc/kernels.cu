@@ -1,17 +1,21 @@
-// CUDA kernels of the FIND passes (FP64 complex).
+// CUDA kernels of the FIND passes (complex; FP64, float-float or complex64
+// arithmetic on complex128 operands).
 //
 //   k_lead_modes / k_lead_dense  lead self-energy closed form (per energy)
 //   k_assemble    gather M = [U_1 A_12; A_21 U_2] (and Sigma_M) ordered [S, B]
 //                 (Procedures updateBoundaryNodes / updateAdjacentNodes)
-//   k_lu          pivoted LU of M(S,S) in place (one CTA per op and energy;
-//                 FP64 or float-float)
+//   k_lu          pivoted LU of M(S,S) in place, column by column (one CTA
+//                 per op and energy; FP64)
+//   k_lu_panel    the same in float-float, in panels of 4 columns; leaves its
+//                 factors as float-float words for k_trsm
 //   k_trsm        L = M(B,S) M(S,S)^{-1} (Eq. 13) by two triangular sweeps,
-//                 row blocks spread over CTAs (FP64, or float-float)
+//                 row blocks spread over CTAs (FP64, or float-float reading
+//                 complex128 or float-float factors)
 //   k_invert      pivoted Gauss-Jordan inverse of the bordered leaf system
 //                 (in global memory, or held in shared memory when it fits;
 //                 FP64 or float-float)
-//   k_zgemm       grouped complex GEMM (FP64, or complex64 arithmetic in the
-//                 mixed path): U = M(B,B) - L M(S,B) (Eq. 2),
+//   k_zgemm       grouped complex GEMM on 32x32 or 64x64 tiles (FP64,
+//                 float-float, or complex64): U = M(B,B) - L M(S,B) (Eq. 2),
 //                 R = Sigma(B,B) - L Sigma(S,B) + (L Sigma(S,S) - Sigma(B,S)) L^H
 //                 (Eq. 7 regrouped), and the leaf products G_K Sigma_K G_K^H
 //   k_extract     diag G, diag G<, bond currents from the bordered leaves
