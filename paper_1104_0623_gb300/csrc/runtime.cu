@@ -1,14 +1,18 @@
 // C ABI of the FIND library: handle, device workspace, per-level descriptor
 // tables and the launch sequence of one solve.
 //
-// Execution of one pass over a batch of energies (all on the caller's stream):
+// Execution of one pass over a batch of energies (on the caller's stream, the
+// energies split into groups that run on up to 4 streams of the handle):
 //   lead self-energies (closed form, unless given)
-//   upward levels by height:   assemble -> invert M(S,S) -> L -> U (+T) (-> R)
+//   upward levels by height:   assemble -> LU of M(S,S) -> L by two triangular
+//                              sweeps -> U (+T) (-> R)
 //   downward levels by depth:  the same kernels on the complement clusters
 //   leaf level:                assemble K -> invert K -> (G_K Sigma_K, .. G_K^H)
 //                              -> extract diag G, diag G<, bond currents
-// U and R of every cluster stay resident in one workspace allocation laid out
-// [matrix id][energy][b][b]; per-level scratch holds M, Sigma_M, L, T.
+// With FIND_FLAG_GRAPH the pass is captured once per call signature and
+// replayed as a CUDA graph.  U and R of every cluster stay resident in one
+// workspace allocation laid out [matrix id][energy][b][b]; per-level scratch,
+// energy-major, holds M, Sigma_M, L, T and the pivots.
 #include "../../include/find.h"
 #include "kernels.cuh"
 #include "plan.hpp"
