@@ -89,9 +89,11 @@ class Find:
             pass
 
     # -- helpers
-    def _stream(self, stream):
+    def _stream(self, stream, nE=1):
         if stream is not None:
             return stream
+        if nE == 0:  # the library returns before any device work
+            return None
         import torch
         return torch.cuda.current_stream(self.device).cuda_stream
 
@@ -110,7 +112,7 @@ class Find:
         nE = int(E.shape[0])
         out = self._out(E, (nE, self.n), np.complex128) if out is None else out
         find_solve_diag(self.handle, _ptr(E, "complex128"), nE, _ptr(sigmaL, "complex128"),
-                        _ptr(sigmaR, "complex128"), _ptr(out, "complex128"), self._stream(stream))
+                        _ptr(sigmaR, "complex128"), _ptr(out, "complex128"), self._stream(stream, nE))
         return out
 
     def solve_lesser(self, E, fL=1.0, fR=0.0, sigmaL=None, sigmaR=None, sigma_lesser_diag=None,
@@ -129,7 +131,7 @@ class Find:
         find_solve_lesser(self.handle, _ptr(E, "complex128"), nE, _ptr(sigmaL, "complex128"),
                           _ptr(sigmaR, "complex128"), fL, fR, _ptr(sigma_lesser_diag, "complex128"),
                           per_e, _ptr(dG, "complex128"), _ptr(dGl, "complex128"),
-                          _ptr(J, "float64"), self._stream(stream))
+                          _ptr(J, "float64"), self._stream(stream, nE))
         return dG, dGl, J
 
     def profile(self, enable=True):

@@ -63,6 +63,17 @@ def test_create_rejects_unknown_flags(F):
     ok.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed_ff"])
+def test_empty_energy_list_is_a_no_op(F, precision):
+    # nE = 0 returns before any device work: empty outputs, no error
+    f = F.Find(6, 9, stencil=9, tp=0.2, precision=precision)
+    E = np.zeros(0, np.complex128)
+    G, Gl, J = f.solve_lesser(E)
+    assert G.shape == (0, 54) and Gl.shape == (0, 54) and J.shape == (0, f.n_bonds)
+    assert f.solve_diag(E).shape == (0, 54)
+    f.close()
+
+
 def test_solve_rejects_null_outputs(F):
     f = F.Find(4, 4)
     with pytest.raises(F.FindError) as ei:

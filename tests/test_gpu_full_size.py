@@ -1,6 +1,6 @@
 """The 256x1024 9-point mesh (t = 1, t' = 0.2, V ~ U[-1, 1], seed 1109) at
 full size, in the launch configuration of the benchmark: leaf 8, 32 energies
-per call.
+per call in one energy group.
 
 * sampled nodes against the refined definition of G and G< (banded LU with
   extended-precision refinement, tests/golden/c5_refined_samples.txt, written
@@ -66,7 +66,7 @@ def batch_energies():
 def test_c5_sampled_nodes_against_refined_definition(F, precision):
     norms, rows = read_golden()
     idx, Es = batch_energies()
-    f = F.Find.from_mesh(W.c5(), leaf=8, max_batch=BATCH, precision=precision)
+    f = F.Find.from_mesh(W.c5(), leaf=8, max_batch=BATCH, energy_group=BATCH, precision=precision)
     G, Gl, _ = [None if x is None else x.cpu().numpy() for x in f.solve_lesser(tcplx(Es), bonds=False)]
     f.close()
     worst = {}
@@ -89,7 +89,7 @@ def test_c5_sampled_nodes_against_refined_definition(F, precision):
 def test_c5_eta_identity_and_continuity_all_energies(F):
     mesh = W.c5()
     _, Es = batch_energies()
-    f = F.Find.from_mesh(mesh, leaf=8, max_batch=BATCH, precision="mixed_ff")
+    f = F.Find.from_mesh(mesh, leaf=8, max_batch=BATCH, energy_group=BATCH, precision="mixed_ff")
     G, Gl, J = [x.cpu().numpy() for x in f.solve_lesser(tcplx(Es))]
     eta = Es[0].imag
     G2, Gl2, _ = [None if x is None else x.cpu().numpy()
@@ -115,7 +115,8 @@ def test_c5_eta_identity_and_continuity_all_energies(F):
 def test_c5_clean_wire_closed_form_all_energies(F):
     mesh = W.Mesh(256, 1024, 9, 1.0, 0.2, 0.0, 0.0, 1109)
     _, Es = batch_energies()
-    f = F.Find.from_mesh(mesh, V=np.zeros(mesh.n), leaf=8, max_batch=BATCH, precision="mixed_ff")
+    f = F.Find.from_mesh(mesh, V=np.zeros(mesh.n), leaf=8, max_batch=BATCH, energy_group=BATCH,
+                         precision="mixed_ff")
     G, Gl, _ = [None if x is None else x.cpu().numpy() for x in f.solve_lesser(tcplx(Es), bonds=False)]
     f.close()
     for k, E in enumerate(Es):
