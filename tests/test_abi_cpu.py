@@ -63,6 +63,18 @@ def test_create_rejects_unknown_flags(F):
     ok.close()
 
 
+def test_largest_block_limit(F):
+    # a bordered leaf system of 2020 nodes (the 1000-wide dense contact
+    # columns) is accepted; 2100-wide contacts exceed the 2048-node blocks
+    # the kernels are built for and are refused at create, not at solve
+    f = F.Find(1000, 4)
+    assert f.stats.max_kn == 2020
+    f.close()
+    with pytest.raises(F.FindError) as ei:
+        F.Find(2100, 4)
+    assert ei.value.code == 1 and "2048" in str(ei.value)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed_ff"])
 def test_empty_energy_list_is_a_no_op(F, precision):
     # nE = 0 returns before any device work: empty outputs, no error
