@@ -106,6 +106,7 @@ class Server:
         self.active: Dict[int, dict] = {}
         self.jobs: collections.deque = collections.deque()
         self.plans: "collections.OrderedDict" = collections.OrderedDict()  # key -> [plan, bytes, users, lock]
+        self.building = set()  # mesh keys whose plan a thread is building (lock released)
         self.results: Dict[int, Result] = {}
         self.max_active = 0
         self.stop = False
@@ -113,14 +114,25 @@ class Server:
 
     # -- plan cache
     def _plan_for(self, mesh, energies=None):
-        """Cached plan of a mesh, or None if its footprint does not fit now.
-        Called with self.lock held."""
+        """Cached plan of a mesh, or None if it is not ready or its footprint
+        does not fit now.  Called with self.lock held; a plan that is not
+        cached is built (and tuned, with a tuner) with the lock released, so
+        running requests keep being served meanwhile, and only one thread
+        builds a given mesh's plan."""
         key = mesh_key(mesh)
         if key in self.plans:
             self.plans.move_to_end(key)
             return self.plans[key]
-        plan = self.backend.make_plan(mesh, energies)
-        need = self.backend.plan_bytes(plan)
+        if key in self.building:
+            return None
+        self.building.add(key)
+        self.lock.release()
+        try:
+            plan = self.backend.make_plan(mesh, energies)
+            need = self.backend.plan_bytes(plan)
+        finally:
+            self.lock.acquire()
+            self.building.discard(key)
         used = sum(p[1] for p in self.plans.values())
         for k in list(self.plans.keys()):
             if used + need <= self.mem_budget:
@@ -141,9 +153,13 @@ class Server:
             req = self.pending[0]
             entry = self._plan_for(req.mesh, req.energies)
             if entry is None:
-                if not self.active:
+                if mesh_key(req.mesh) in self.building:
+                    return  # another thread is building its plan
+                if not self.active and self.pending and self.pending[0] is req:
                     raise RuntimeError(f"request {req.rid} does not fit the device memory budget")
                 return
+            if not self.pending or self.pending[0] is not req:
+                continue  # the queue moved while the plan was being built
             self.pending.popleft()
             entry[2] += 1
             n = len(req.energies)

@@ -75,3 +75,41 @@ def test_results_latencies_and_admission():
     s = summarize(res)
     assert s["requests"] == 9 and s["p99_s"] >= s["p50_s"] > 0
     srv.close()
+
+
+class SlowPlanBackend(FakeBackend):
+    """Plans take 0.2 s to build (as with autotuning); solves are timestamped."""
+
+    def __init__(self, budget):
+        super().__init__(budget)
+        self.solves = []      # (start time, mesh key)
+        self.builds = []      # (start, end, mesh key)
+
+    def make_plan(self, mesh, energies=None):
+        t = time.perf_counter()
+        time.sleep(0.2)
+        self.builds.append((t, time.perf_counter(), mesh_key(mesh)))
+        return super().make_plan(mesh, energies)
+
+    def solve(self, plan, energies, stream):
+        with self.mu:
+            self.solves.append((time.perf_counter(), plan[1]))
+        return super().solve(plan, energies, stream)
+
+
+def test_plans_are_built_without_stalling_running_requests():
+    be = SlowPlanBackend(budget=1e9)
+    srv = Server(be, slots=2, chunk=1)
+    a = Request(0, 0.0, W.Mesh(4, 5, 5, seed=1), W.energy_grid(0.1, 3.0, 200))
+    b = Request(1, 0.05, W.Mesh(6, 5, 5, seed=2), W.energy_grid(0.1, 3.0, 4))
+    res = srv.run([a, b])
+    srv.close()
+    for r, req in zip(res, (a, b)):
+        n = req.mesh.nx * req.mesh.ny
+        assert np.array_equal(r.diagG, np.outer(req.energies, np.arange(1, n + 1)))
+    # while the second mesh's plan was being built, the first request's
+    # chunks kept running
+    t0, t1, kb = next(x for x in be.builds if x[2] == mesh_key(b.mesh))
+    during = [t for t, k in be.solves if k == mesh_key(a.mesh) and t0 < t < t1]
+    assert len(during) >= 5
+    assert len(be.builds) == 2   # each plan built once
