@@ -28,6 +28,10 @@ The steps follow the paper in its own order and notation:
               is G_K Sigma_K G_K^H with Sigma_K = [R_Cbar S(Bb,C); S(C,Bb) S(C,C)].
     Bond currents use the neighbour entries of that bordered G<.
 
+Optionally (symmetric=True, Sec. 4.2) the eliminations use the symmetric
+factorisation M(S,S) = L D L^T with Bunch-Kaufman pivoting instead of the LU
+(eliminate_symmetric); A must equal A^T.
+
 Readings taken where the paper is silent: the tree bisects the longer side
 (ties split y; the first half gets floor(len/2)) until both sides are <= leaf;
 B sets are computed on the structural graph of A, which includes the dense
@@ -118,6 +122,37 @@ def eliminate(M: np.ndarray, Sg: np.ndarray, s: int):
     return U, R
 
 
+def eliminate_symmetric(M: np.ndarray, Sg: np.ndarray, s: int):
+    """The same elimination for complex symmetric M (A = A^T), by the
+    symmetric factorisation of Sec. 4.2 (optimisation for symmetry):
+
+        M(S,S) = Lf D Lf^T       (LDL^T with Bunch-Kaufman diagonal pivoting:
+                                   D has 1x1 and 2x2 blocks; Lf is lower
+                                   triangular up to the pivot permutation)
+        W = Lf^{-1} M(S,B)
+        U = M(B,B) - W^T D^{-1} W                     (Eq. 2, as in Sec. 4.2)
+        L = M(B,S) M(S,S)^{-1} = (Lf^{-T} D^{-1} W)^T (Eq. 13; M(B,S) = M(S,B)^T)
+        R as in Eq. (7).
+
+    Plain transposes throughout (complex symmetric, not Hermitian)."""
+    if s == 0:
+        return M.copy(), Sg.copy()
+    from scipy.linalg import ldl, solve_triangular
+    MSS, MSB, MBB = M[:s, :s], M[:s, s:], M[s:, s:]
+    lu, d, perm = ldl(MSS, lower=True, hermitian=False)
+    W = solve_triangular(lu[perm], MSB[perm], lower=True, unit_diagonal=True)
+    DW = np.linalg.solve(d, W)
+    U = MBB - W.T @ DW
+    # L^T = Lf^{-T} D^{-1} W with Lf = lu, whose rows perm form a unit lower
+    # triangle T: Lf^{-T} = P^T T^{-T} applied as a solve with T^T, unpermuted
+    Lt = np.empty_like(DW)
+    Lt[perm] = solve_triangular(lu[perm].T, DW, lower=False, unit_diagonal=True)
+    L = Lt.T
+    LH = L.conj().T
+    R = Sg[s:, s:] - L @ Sg[:s, s:] - Sg[s:, :s] @ LH + L @ Sg[:s, :s] @ LH
+    return U, R
+
+
 def _reorder(nodes: np.ndarray, keep: np.ndarray):
     """Permutation of ``nodes`` into [S, keep]: S = nodes not kept (in their
     given order), followed by the kept nodes in the order of ``keep``."""
@@ -134,8 +169,16 @@ class FindOracle:
     """FIND for one matrix A and one Sigma (any values on the FIND pattern)."""
 
     def __init__(self, A, Sl, nx: int, ny: int, pattern=None, leaf: int = 8,
-                 tie: str = "y"):
+                 tie: str = "y", symmetric: bool = False):
         self.A = sp.csr_matrix(A, dtype=np.complex128)
+        # symmetric: eliminate with the LDL^T form (eliminate_symmetric),
+        # which reads one triangle of each block and M(S,B) for M(B,S), i.e.
+        # uses the symmetric part of A; A must equal A^T up to rounding (the
+        # closed-form lead Sigma = Phi diag(sigma) Phi^T is symmetric only to
+        # the last bit).  Property 1 keeps every U symmetric.
+        self.symmetric = symmetric
+        if symmetric and abs(self.A - self.A.T).max() > 1e-13 * abs(self.A).max():
+            raise ValueError("the symmetric elimination needs A = A^T")
         self.Sl = sp.csr_matrix(Sl, dtype=np.complex128)
         self.A.sum_duplicates()
         self.Sl.sum_duplicates()
@@ -180,7 +223,8 @@ class FindOracle:
 
     def _eliminate_onto(self, nodes, M, Sg, keep):
         perm, s = _reorder(nodes, keep)
-        return eliminate(M[np.ix_(perm, perm)], Sg[np.ix_(perm, perm)], s)
+        elim = eliminate_symmetric if self.symmetric else eliminate
+        return elim(M[np.ix_(perm, perm)], Sg[np.ix_(perm, perm)], s)
 
     # -- Procedure updateBoundaryNodes
     def update_boundary_nodes(self, c: int):
@@ -288,12 +332,12 @@ class FindOracle:
 
 
 def find_outputs(problem, E, fL=1.0, fR=0.0, leaf=8, tie="y", bonds=True,
-                 sigL=None, sigR=None, diag_lesser=None):
+                 sigL=None, sigR=None, diag_lesser=None, symmetric=False):
     """diag G, diag G< and bond currents J of a MeshProblem at energy E."""
     from .dense import bond_list, bond_current_from
 
     A, Sl = problem.assemble(E, fL, fR, sigL, sigR, diag_lesser)
-    f = FindOracle(A, Sl, problem.nx, problem.ny, problem.pattern, leaf, tie)
+    f = FindOracle(A, Sl, problem.nx, problem.ny, problem.pattern, leaf, tie, symmetric)
     if not bonds:
         dG, dGl, _ = f.run()
         return dG, dGl, None, f
