@@ -66,7 +66,7 @@ def test_nonsymmetric_A_is_refused():
         find.FindOracle(A, S, 6, 9, problem.find_pattern(6, 9, 5), 3, symmetric=True)
 
 
-@pytest.mark.filterwarnings("ignore:.*imaginary parts of the diagonal")
+@pytest.mark.filterwarnings(r"ignore:scipy\.linalg\.ldl")
 def test_hermitian_transpose_mistake_is_caught(monkeypatch):
     from scipy.linalg import ldl, solve_triangular
 
