@@ -101,6 +101,20 @@ typedef struct {
                                product: 64x64 unless that pads more area than
                                the 32x32 tiling, by more than 20 % for
                                float-float and complex64, at all for FP64      */
+  int tc_slices;            /* products that must match FP64 (every product of
+                               FIND_FP64, the top levels of the mixed paths):
+                               0 = FP64 on the CUDA cores (the default); 1..12
+                               = on the tensor cores with this many digit
+                               planes per operand (10 or more to match an FP64
+                               product on operands of wide dynamic range)      */
+  int tc_slices_mixed;      /* digit planes of the products the mixed paths run
+                               below their top levels: 0 = 9 (about 2^-53
+                               relative to the largest entries of the row of A
+                               and the column of op(B)); at most 12            */
+  int tc_min;               /* a product runs on the tensor cores when its
+                               rows, columns and inner dimension are all at
+                               least this (and its padding to the 128 x 128 x
+                               64 tiles wastes little enough); 0 = 32          */
 } find_desc;
 
 /* find_desc.flags.  With the closed-form leads A = A^T, so every U is complex
@@ -112,7 +126,23 @@ typedef struct {
    dominates).
      FIND_FLAG_FULL_U  both triangles on every path
      FIND_FLAG_SYM_U   one triangle on FIND_FP64 too (ignored with FULL_U)  */
-enum { FIND_FLAG_FULL_U = 1, FIND_FLAG_SYM_U = 2, FIND_FLAG_GRAPH = 4 };
+enum { FIND_FLAG_FULL_U = 1, FIND_FLAG_SYM_U = 2, FIND_FLAG_GRAPH = 4, FIND_FLAG_NO_TC = 8 };
+/* Tensor-core products.  The Schur-update products (Eq. 2, Eq. 7) and the
+   leaf products G_K Sigma_K G_K^H run by default on the bf16 tensor cores
+   (tcgen05) through an error-free digit-plane split of the complex128
+   operands (Ozaki et al. 2012): each row of A and each column of op(B) is
+   scaled by a power of two and cut into signed base-64 digits; the digit
+   products of one weight are accumulated exactly in FP32 tensor memory and
+   summed as exact integers.  The error of a product entry is relative to the
+   largest entries of its row of A and column of op(B) (about 2^-(6 planes)),
+   not to the entries it sums, so operands whose rows decay over many decades
+   (Green's-function blocks at energies near an inner resonance) need more
+   planes than their FP64 precision suggests: on the 256x1024 mesh 9 planes
+   left the FP64 path 200 times less accurate than FP64 products at the worst
+   energy, so FP64 products stay on the CUDA cores unless tc_slices asks
+   otherwise, while the mixed paths (bar 1e-5) take 9 planes.
+   FIND_FLAG_NO_TC keeps every product on the CUDA-core kernels (FP64 or
+   float-float). */
 /* FIND_FLAG_GRAPH: find_solve_diag / find_solve_lesser capture the device work
    of a pass (closed-form lead Sigma and every level's launches, over all
    energy-group streams) into a CUDA graph the first time a call signature is
@@ -233,11 +263,13 @@ int find_solve_diag_static(find_handle* h, const double* E, int nE,
  * solve's stream around every launch while profiling is on).  Kernel
  * classes: "lead", "assemble", "invert", "lu", "trsm", "zgemm32",
  * "zgemm64", "extract", "cgemm32", "cgemm64", "ffgemm32", "ffgemm64",
- * "fftrsm", "fflu", "ffinvert" (z: FP64, c: complex64, ff: float-float
- * arithmetic; 32/64: tile size).  flops are the algorithmic real flops of the
- * launches (GEMM: 8 m n k per op and energy; LU: 8 s^3 / 3; triangular
- * solves: 8 s^2 b; leaf inversion: 8 n^3), bytes the algorithmic DRAM bytes
- * of the gather/extract kernels (blocks written plus source blocks read). */
+ * "fftrsm", "fflu", "ffinvert", "tcsplit", "tcgemm" (z: FP64, c: complex64,
+ * ff: float-float arithmetic; 32/64: tile size; tc: the tensor-core products,
+ * split into digit planes, then multiplied).  flops are the algorithmic real
+ * flops of the launches (GEMM: 8 m n k per op and energy; LU: 8 s^3 / 3;
+ * triangular solves: 8 s^2 b; leaf inversion: 8 n^3), bytes the algorithmic
+ * DRAM bytes of the gather/extract kernels (blocks written plus source blocks
+ * read) and of the plane split (operands read, planes written). */
 typedef struct {
   char name[16];
   int launches;

@@ -22,6 +22,7 @@ FIND_MIXED_FF = 2
 FIND_FLAG_FULL_U = 1
 FIND_FLAG_SYM_U = 2
 FIND_FLAG_GRAPH = 4
+FIND_FLAG_NO_TC = 8
 
 STATUS_NAMES = {0: "FIND_OK", 1: "FIND_EINVAL", 2: "FIND_ENOMEM", 3: "FIND_ESINGULAR",
                 4: "FIND_ETIMEOUT", 5: "FIND_ECUDA"}
@@ -39,7 +40,8 @@ class find_desc(ctypes.Structure):
                 ("max_batch", ctypes.c_int), ("fp64_top_levels", ctypes.c_int),
                 ("energy_group", ctypes.c_int), ("invert_smem", ctypes.c_int),
                 ("sigma_c64_depth", ctypes.c_int), ("flags", ctypes.c_int),
-                ("gemm_small_max", ctypes.c_int)]
+                ("gemm_small_max", ctypes.c_int), ("tc_slices", ctypes.c_int),
+                ("tc_slices_mixed", ctypes.c_int), ("tc_min", ctypes.c_int)]
 
 
 class find_plan_stats(ctypes.Structure):
@@ -139,11 +141,11 @@ def find_profile(handle: int, enable: bool) -> None:
 
 def find_profile_read(handle: int):
     """Per-kernel-class dicts: name, launches, ms, flops, bytes."""
-    arr = (find_kernel_stat * 16)()
+    arr = (find_kernel_stat * 32)()
     cnt = ctypes.c_int()
-    _check(load().find_profile_read(handle, arr, 16, ctypes.byref(cnt)), handle)
+    _check(load().find_profile_read(handle, arr, 32, ctypes.byref(cnt)), handle)
     return [dict(name=arr[k].name.decode(), launches=arr[k].launches, ms=arr[k].ms,
-                 flops=arr[k].flops, bytes=arr[k].bytes) for k in range(cnt.value)]
+                 flops=arr[k].flops, bytes=arr[k].bytes) for k in range(min(cnt.value, 32))]
 
 
 def find_destroy(handle: int) -> None:

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "plan.hpp"  // Pos, LeafBond
@@ -119,5 +120,82 @@ void launch_extract(const ExtractOp* ops, int nops, const LeafBond* bonds, const
                     int64_t n_nodes, int64_t n_bonds, int nE, cudaStream_t st, int e_off = 0);
 
 constexpr int kMaxInvert = 2048;  // largest block the in-CTA inversion accepts
+
+// ---- tensor-core products (tc_gemm.cu): D = beta C + a1 A1 op(B1) + a2 A2 op(B2)
+// computed from bf16 digit planes of the operands (see tc_gemm.cu).
+struct TcOp {
+  int m, n;              // output rows, columns
+  int k1, k2;            // inner dimensions of the two products (k2 = 0: none)
+  int k1p, kp;           // k1 padded to 64 (offset of the second product), total padded K
+  int mt, tiles_n;       // 128-row and 128-column tiles
+  int tile0;             // first tile of this op in the launch
+  int nsl, nexact;       // digit planes per operand; exactly accumulated diagonals
+  int arow, brow;        // first plane row of A / op(B) in the slab (per energy)
+  int ascale, bscale;    // first exponent of the rows of A / columns of op(B)
+  const cplx* A1; int lda1; int64_t sa1; int neg1;
+  const cplx* B1; int ldb1; int64_t sb1; int opb1;
+  const cplx* A2; int lda2; int64_t sa2; int neg2;
+  const cplx* B2; int ldb2; int64_t sb2; int opb2;
+  const cplx* C; int ldc; int64_t sc; double beta;
+  cplx* D; int ldd; int64_t sd;
+};
+
+// Digit planes and exponents of one launch, energy 0; energy e at + e * estride.
+// A plane (s, part) of op o holds rows o.arow + (2 s + part) * 128 o.mt ...,
+// each `pitch` bf16 long (K-contiguous).
+struct TcSlab {
+  unsigned short* a;
+  unsigned short* b;
+  int64_t pitch;          // bf16 per plane row
+  int64_t plane_estride;  // bf16 between energies
+  int* scale;
+  int64_t scale_estride;  // ints between energies
+};
+
+struct TcLaunch {
+  TcSlab slab;
+  int scale_ints;          // exponents per energy
+  alignas(64) unsigned char mapA[128];  // CUtensorMap of the A planes (3D: K, row, energy)
+  alignas(64) unsigned char mapB[128];
+};
+
+// Encodes the 3D tensor map (K pitch_elems, rows, energies; energy stride in
+// bytes) of a bf16 plane slab with 64 x 128 boxes and the 128-byte swizzle.
+// Returns 0 on success.
+int tc_encode_map(void* map_out, const void* base, int64_t pitch_elems, int64_t rows,
+                  int64_t energies, int64_t estride_bytes);
+int tc_tile_m();
+int tc_tile_n();
+int tc_tile_k();
+int tc_smem_bytes();
+
+// Host tables of one tensor-core launch: ops (with their plane rows, exponent
+// offsets and tiles assigned by tc_add_op), work items and the tile -> op map.
+struct TcBuild {
+  std::vector<TcOp> ops;
+  std::vector<int4> scale_items, row_items, col_items;
+  std::vector<int> tile_op;
+  int64_t rowsA = 0, rowsB = 0, pitch = 0;
+  int scale_ints = 0;
+};
+// Adds an op given m, n, k1, k2, nsl, nexact and its operands.
+void tc_add_op(TcBuild& b, TcOp op);
+// Bytes per energy of the launch's planes and exponents, and their offsets.
+int64_t tc_slab_bytes(const TcBuild& b, int64_t* offA, int64_t* offB, int64_t* offS);
+// Slab bytes one op alone needs (planes and exponents, per energy).
+int64_t tc_op_slab_bytes(int m, int n, int k1, int k2, int nsl);
+// The two halves of launch_tc_gemm: exponents and digit planes; products.
+void launch_tc_split(const TcLaunch& L, const TcOp* ops, const int4* scale_items, int nscale,
+                     const int4* row_items, int nrow, const int4* col_items, int ncol, int nE,
+                     cudaStream_t st, int e_off = 0);
+void launch_tc_mma(const TcLaunch& L, const TcOp* ops, const int* tile_op, int ntiles, int* status,
+                   int nE, cudaStream_t st, int e_off = 0);
+// Splits the operands of every op into digit planes and runs the products.
+// items (one per CTA): scale (op, kind | part << 4, i0, k0), rows (op, side,
+// r0), cols (op, part, j0, k0); status[1] records a bounded wait that ran out.
+void launch_tc_gemm(const TcLaunch& L, const TcOp* ops, const int4* scale_items, int nscale,
+                    const int4* row_items, int nrow, const int4* col_items, int ncol,
+                    const int* tile_op, int ntiles, int* status, int nE, cudaStream_t st,
+                    int e_off = 0);
 
 }  // namespace findgb

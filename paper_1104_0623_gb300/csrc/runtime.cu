@@ -71,11 +71,22 @@ enum Arith { kFP64 = 0, kC64 = 1, kFF = 2 };
 // One GEMM stage of a level: its ops and the tile maps of the six launch
 // classes 2 * arith + big: [FP64 small, FP64 big, complex64 small, complex64
 // big, float-float small, float-float big].
+// The tensor-core products of a stage, in chunks whose digit planes fit the
+// level's plane region (each chunk is one split and one product launch; the
+// chunks of a stage run one after the other on the region).
+struct TcChunk {
+  findgb::TcLaunch L;
+  size_t ops = 0, sitems = 0, ritems = 0, citems = 0, tmap = 0;  // arena offsets
+  int nsitems = 0, nritems = 0, ncitems = 0, ntiles = 0;
+  double fl = 0, by = 0;  // algorithmic flops and split bytes per energy
+};
+
 struct Stage {
   size_t ops = 0;
   size_t map[6] = {0, 0, 0, 0, 0, 0};  // arena offsets
   int nmap[6] = {0, 0, 0, 0, 0, 0};
   double fl[6] = {0, 0, 0, 0, 0, 0};   // algorithmic flops per energy of each class
+  std::vector<TcChunk> tc;
 };
 
 struct Level {
@@ -133,7 +144,7 @@ struct find_handle {
   bool prof = false;
   std::vector<cudaEvent_t> ev_free;
   std::vector<Pending> pending;
-  find_kernel_stat stats[15];
+  find_kernel_stat stats[17];
   // tables for the fixed device scratch
   StaticView sview;
   // streams and events of the concurrent energy groups of one pass
@@ -210,6 +221,71 @@ void add_gemm(findgb::GemmOp g, std::vector<findgb::GemmOp>& ops, std::vector<in
   for (int t = 0; t < tm * tn; ++t) map.push_back(id);
 }
 
+int rup(int x, int m) { return (x + m - 1) / m * m; }
+
+// Digit planes of the tensor-core product that replaces GEMM g of arithmetic
+// a, or 0 to keep g on the CUDA-core kernels: complex64 products stay there;
+// so do products below tc_min in any dimension, products whose inner
+// dimension exceeds the exact-accumulation limit of the planes (1024), and
+// products whose padding to the 128 x 128 x 64 tiles wastes more than the
+// tensor cores gain over the CUDA-core kernel of the same arithmetic
+// (measured: about 12x over FP64, 5x over float-float).  Products that must
+// match FP64 use the tensor cores only when tc_slices asks for it.
+int tc_planes(const find_handle* h, const findgb::GemmOp& g, Arith a) {
+  if ((h->desc.flags & FIND_FLAG_NO_TC) || a == kC64) return 0;
+  const int k2 = g.A2 ? g.k2 : 0, kt = g.k + k2;
+  const int mn = h->desc.tc_min > 0 ? h->desc.tc_min : 32;
+  if (g.m < mn || g.n < mn || kt < mn || kt > 1024) return 0;
+  const double used = (double)g.m * g.n * kt;
+  const double padded = (double)rup(g.m, findgb::tc_tile_m()) * rup(g.n, findgb::tc_tile_n()) *
+                        (rup(g.k, findgb::tc_tile_k()) + rup(k2, findgb::tc_tile_k()));
+  if (used < (a == kFP64 ? 0.10 : 0.25) * padded) return 0;
+  if (a == kFP64) return h->desc.tc_slices;  // 0: FP64 products stay on the CUDA cores
+  return h->desc.tc_slices_mixed > 0 ? h->desc.tc_slices_mixed : 9;
+}
+
+findgb::TcOp tc_from_gemm(const findgb::GemmOp& g, int nsl) {
+  findgb::TcOp t;
+  std::memset(&t, 0, sizeof(t));
+  t.m = g.m; t.n = g.n; t.k1 = g.k; t.k2 = g.A2 ? g.k2 : 0;
+  // exactly accumulated diagonals: every one up to 5 (a diagonal of q + 1
+  // pairs stays exact for (q + 1) K <= 8192, and the fixed-point sum of the
+  // epilogue holds 6 of them); the rest share the last, rounded group
+  t.nsl = nsl; t.nexact = std::min(nsl, 6);
+  t.A1 = g.A; t.lda1 = g.lda; t.sa1 = g.sa; t.neg1 = g.alpha < 0.0;
+  t.B1 = g.B; t.ldb1 = g.ldb; t.sb1 = g.sb; t.opb1 = g.opb;
+  if (g.A2) {
+    t.A2 = g.A2; t.lda2 = g.lda2; t.sa2 = g.sa2; t.neg2 = g.alpha2 < 0.0;
+    t.B2 = g.B2; t.ldb2 = g.ldb2; t.sb2 = g.sb2; t.opb2 = g.opb2;
+  }
+  t.C = g.C; t.ldc = g.ldc; t.sc = g.sc; t.beta = g.beta;
+  t.D = g.D; t.ldd = g.ldd; t.sd = g.sd;
+  return t;
+}
+
+// Plane bytes per energy a chunk may take; a single larger op gets a chunk of
+// its own.
+constexpr int64_t kTcChunkBudget = int64_t(256) << 20;
+
+// Groups the ops of a stage into chunks (the same for the same shapes, so the
+// sizing and the real table builds agree).
+std::vector<findgb::TcBuild> tc_chunks(const std::vector<findgb::TcOp>& ops) {
+  std::vector<findgb::TcBuild> out;
+  int64_t rows = 0, kp = 0, ints = 0;
+  for (const auto& op : ops) {
+    const int64_t r = 2LL * op.nsl * (rup(op.m, findgb::tc_tile_m()) + rup(op.n, findgb::tc_tile_n()));
+    const int64_t k = rup(op.k1, findgb::tc_tile_k()) + rup(op.k2, findgb::tc_tile_k());
+    const int64_t in = rup(op.m, findgb::tc_tile_m()) + rup(op.n, findgb::tc_tile_n());
+    if (out.empty() || (rows > 0 && (rows + r) * std::max(kp, k) * 2 + 4 * (ints + in) > kTcChunkBudget)) {
+      out.emplace_back();
+      rows = 0; kp = 0; ints = 0;
+    }
+    rows += r; kp = std::max(kp, k); ints += in;
+    findgb::tc_add_op(out.back(), op);
+  }
+  return out;
+}
+
 findgb::GemmOp gemm0() {
   findgb::GemmOp g;
   std::memset(&g, 0, sizeof(g));
@@ -251,14 +327,14 @@ struct Bounds {
 // Builds every level's descriptor tables into `ar`, with device pointers
 // computed from `base` (the workspace address; 0 for sizing).
 void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batch, bool lesser,
-                  Arena& ar, std::vector<Level>& levels, int64_t& scratch_elems, Bounds* bc = nullptr) {
+                  Arena& ar_out, std::vector<Level>& levels_out, int64_t& scratch_elems,
+                  Bounds* bc = nullptr, int* map_err = nullptr) {
   const findgb::Plan& p = h->plan;
   cplx* U = reinterpret_cast<cplx*>(base + L.U);
   cplx* R = lesser ? reinterpret_cast<cplx*>(base + L.R) : nullptr;
   cplx* S0 = reinterpret_cast<cplx*>(base + L.scratch);
   auto umat = [&](int id) { return id < 0 ? (cplx*)nullptr : U + p.mat_off[id] * batch; };
   auto rmat = [&](int id) { return (id < 0 || !R) ? (cplx*)nullptr : R + p.mat_off[id] * batch; };
-  levels.clear();
   scratch_elems = 0;
   const bool mixed = h->desc.precision == FIND_MIXED || h->desc.precision == FIND_MIXED_FF;
   const bool ff_all = h->desc.precision == FIND_MIXED_FF;
@@ -307,7 +383,69 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
   }
   escr = (escr + 15) & ~int64_t(15);  // keep every energy's region 256-byte aligned
 
-  auto elim_level = [&](const std::vector<findgb::ElimOp>& ops) {
+  // The digit planes of a level's tensor-core products live in each energy's
+  // scratch region after the level's op slots; escr is sized by a dry build.
+  auto finish_tc = [&](Level& lv, std::vector<findgb::TcOp>* tcq, int nst, int64_t slot_end, Arena& arx,
+                       bool dry, int64_t& need) {
+    const int64_t off = (slot_end + 63) & ~int64_t(63);  // 1 KiB aligned within the region
+    unsigned char* region = reinterpret_cast<unsigned char*>(S0 + off);
+    for (int k = 0; k < nst; ++k) {
+      for (auto& b : tc_chunks(tcq[k])) {
+        int64_t oA = 0, oB = 0, oS = 0;
+        const int64_t bytes = findgb::tc_slab_bytes(b, &oA, &oB, &oS);
+        need = std::max(need, off + (bytes + 15) / 16);
+        if (dry) continue;
+        TcChunk c;
+        c.L.slab.a = reinterpret_cast<unsigned short*>(region + oA);
+        c.L.slab.b = reinterpret_cast<unsigned short*>(region + oB);
+        c.L.slab.pitch = b.pitch;
+        c.L.slab.plane_estride = escr * (int64_t)(sizeof(cplx) / 2);
+        c.L.slab.scale = reinterpret_cast<int*>(region + oS);
+        c.L.slab.scale_estride = escr * (int64_t)(sizeof(cplx) / 4);
+        c.L.scale_ints = b.scale_ints;
+        if (bc && bc->err.empty()) {
+          if ((off * 16 + bytes) > escr * 16) bc->err = "tensor-core planes outside the energy's scratch";
+          for (const auto& t : b.ops) {
+            bc->block(t.A1, t.m, t.k1, t.lda1, t.sa1, batch, "tc A1");
+            if (t.opb1 == 0) bc->block(t.B1, t.k1, t.n, t.ldb1, t.sb1, batch, "tc B1");
+            else bc->block(t.B1, t.n, t.k1, t.ldb1, t.sb1, batch, "tc B1^H");
+            if (t.A2) {
+              bc->block(t.A2, t.m, t.k2, t.lda2, t.sa2, batch, "tc A2");
+              if (t.opb2 == 0) bc->block(t.B2, t.k2, t.n, t.ldb2, t.sb2, batch, "tc B2");
+              else bc->block(t.B2, t.n, t.k2, t.ldb2, t.sb2, batch, "tc B2^H");
+            }
+            if (t.C) bc->block(t.C, t.m, t.n, t.ldc, t.sc, batch, "tc C");
+            bc->block(t.D, t.m, t.n, t.ldd, t.sd, batch, "tc D");
+            if (t.nexact > 6 || t.k1 + t.k2 > 1024) bc->err = "tc op outside the exact range";
+          }
+        }
+        if (map_err && base) {
+          if (findgb::tc_encode_map(c.L.mapA, c.L.slab.a, b.pitch, b.rowsA, batch, escr * 16) ||
+              findgb::tc_encode_map(c.L.mapB, c.L.slab.b, b.pitch, b.rowsB, batch, escr * 16))
+            *map_err = 1;
+        }
+        for (const auto& t : b.ops) {
+          const double kt = t.k1 + t.k2;
+          c.fl += 8.0 * t.m * t.n * kt;
+          c.by += 16.0 * (t.m + t.n) * kt +
+                  2.0 * 2 * t.nsl * ((double)t.mt * 128 + (double)t.tiles_n * 128) * t.kp;
+        }
+        c.ops = arx.put(b.ops);
+        c.sitems = arx.put(b.scale_items);
+        c.ritems = arx.put(b.row_items);
+        c.citems = arx.put(b.col_items);
+        c.tmap = arx.put(b.tile_op);
+        c.nsitems = (int)b.scale_items.size();
+        c.nritems = (int)b.row_items.size();
+        c.ncitems = (int)b.col_items.size();
+        c.ntiles = (int)b.tile_op.size();
+        lv.st[k].tc.push_back(c);
+      }
+    }
+  };
+
+  auto elim_level = [&](const std::vector<findgb::ElimOp>& ops, Arena& arx, std::vector<Level>& lvx,
+                        bool dry, int64_t& need) {
     Level lv;
     std::vector<findgb::AsmOp> asmops;
     std::vector<int> row_op;
@@ -316,6 +454,12 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     std::vector<int> trs_map[2];
     std::vector<findgb::GemmOp> g[2];
     std::vector<int> maps[2][6];
+    std::vector<findgb::TcOp> tcq[2];
+    auto route = [&](const findgb::GemmOp& q, int k, Arith a) {
+      const int nsl = tc_planes(h, q, a);
+      if (nsl > 0 && q.m > 0 && q.n > 0) tcq[k].push_back(tc_from_gemm(q, nsl));
+      else add_gemm(q, g[k], maps[k], &lv.st[k], a, small_max);
+    };
     for (const auto& op : ops) lv.max_s = std::max(lv.max_s, op.s);
     lv.rb = findgb::trsm_rows_per_block(lv.max_s);
     int64_t off = 0;
@@ -385,7 +529,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       q.C = M + (int64_t)s * n + s; q.ldc = n; q.sc = escr; q.beta = 1.0;
       q.D = umat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
       q.sym = 1;  // U is complex symmetric when A is (Property 1)
-      gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], ua, small_max);
+      gemm_ok(q); route(q, 0, ua);
       const int c64_from = h->desc.sigma_c64_depth;
       const Arith sa = !below_top ? kFP64
                        : ((c64_from > 0 && p.cl[op.cluster].depth >= c64_from) ? kC64 : kFF);
@@ -397,7 +541,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         q.B = Sg; q.ldb = n; q.sb = escr;
         q.C = Sg + (int64_t)s * n; q.ldc = n; q.sc = escr; q.beta = -1.0;
         q.D = T; q.ldd = s; q.sd = escr;
-        gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], sa, small_max);
+        gemm_ok(q); route(q, 0, sa);
         // stage 1: R = Sigma(B,B) - L Sigma(S,B) + T L^H     (Eq. 7)
         q = gemm0();
         q.m = b; q.n = b; q.k = s; q.k2 = s;
@@ -412,40 +556,35 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         // mutually consistent: mirroring one triangle was measured to raise
         // the diag G< error from 1e-6 to 1e-2 (complex64) and from 5e-15 to
         // 3e-11 (FP64), so R is computed in full
-        gemm_ok(q); add_gemm(q, g[1], maps[1], &lv.st[1], sa, small_max);
+        gemm_ok(q); route(q, 1, sa);
       }
     }
     lv.nops = (int)ops.size();
-    lv.asmops = ar.put(asmops);
-    lv.row_op = ar.put(row_op);
+    lv.asmops = arx.put(asmops);
+    lv.row_op = arx.put(row_op);
     for (int c = 0; c < 4; ++c) {
-      lv.inv[c] = ar.put(inv[c]);
+      lv.inv[c] = arx.put(inv[c]);
       lv.ninv[c] = (int)inv[c].size();
     }
-    lv.trsm = ar.put(trs);
+    lv.trsm = arx.put(trs);
     for (int c = 0; c < 2; ++c) {
-      lv.trsm_map[c] = ar.put(trs_map[c]);
+      lv.trsm_map[c] = arx.put(trs_map[c]);
       lv.ntrsm[c] = (int)trs_map[c].size();
     }
     lv.nstages = lesser ? 2 : 1;
     for (int k = 0; k < lv.nstages; ++k) {
-      lv.st[k].ops = ar.put(g[k]);
+      lv.st[k].ops = arx.put(g[k]);
       for (int c = 0; c < 6; ++c) {
-        lv.st[k].map[c] = ar.put(maps[k][c]);
+        lv.st[k].map[c] = arx.put(maps[k][c]);
         lv.st[k].nmap[c] = (int)maps[k][c].size();
       }
     }
-    scratch_elems = escr;
-    levels.push_back(lv);
+    finish_tc(lv, tcq, lv.nstages, off, arx, dry, need);
+    lvx.push_back(lv);
   };
 
-  for (const auto& lv : p.up_levels) elim_level(lv);
-  h->n_up = (int)p.up_levels.size();
-  for (const auto& lv : p.dn_levels) elim_level(lv);
-  h->n_dn = (int)p.dn_levels.size();
-
   // leaf level
-  {
+  auto leaf_level = [&](Arena& arx, std::vector<Level>& lvx, bool dry, int64_t& need) {
     Level lv;
     lv.leaf = true;
     std::vector<findgb::AsmOp> asmops;
@@ -453,6 +592,12 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     std::vector<findgb::InvOp> inv[4];
     std::vector<findgb::GemmOp> g[2];
     std::vector<int> maps[2][6];
+    std::vector<findgb::TcOp> tcq[2];
+    auto route = [&](const findgb::GemmOp& q, int k, Arith a) {
+      const int nsl = tc_planes(h, q, a);
+      if (nsl > 0 && q.m > 0 && q.n > 0) tcq[k].push_back(tc_from_gemm(q, nsl));
+      else add_gemm(q, g[k], maps[k], &lv.st[k], a, small_max);
+    };
     std::vector<findgb::ExtractOp> ext;
     int64_t off = 0;
     for (const auto& op : p.leaf_ops) {
@@ -511,14 +656,14 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         // keeps the mixed paths' G< error near that of the complex64 Sigma
         // update alone (complex64 here reached 1e-5 on a 64x128 mesh)
         const Arith la = (mixed && p.cl[op.cluster].depth > top_levels) ? kFF : kFP64;
-        gemm_ok(q); add_gemm(q, g[0], maps[0], &lv.st[0], la, small_max);
+        gemm_ok(q); route(q, 0, la);
         // Q = P G_K^H = G<_K(C, :)
         q = gemm0();
         q.m = op.c; q.n = n; q.k = n;
         q.A = P; q.lda = n; q.sa = escr;
         q.B = M; q.ldb = n; q.sb = escr; q.opb = 1;
         q.D = Q; q.ldd = n; q.sd = escr;
-        gemm_ok(q); add_gemm(q, g[1], maps[1], &lv.st[1], la, small_max);
+        gemm_ok(q); route(q, 1, la);
       }
       findgb::ExtractOp x;
       x.K = M;
@@ -530,24 +675,46 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       ext.push_back(x);
     }
     lv.nops = (int)p.leaf_ops.size();
-    lv.asmops = ar.put(asmops);
-    lv.row_op = ar.put(row_op);
+    lv.asmops = arx.put(asmops);
+    lv.row_op = arx.put(row_op);
     for (int c = 0; c < 4; ++c) {
-      lv.inv[c] = ar.put(inv[c]);
+      lv.inv[c] = arx.put(inv[c]);
       lv.ninv[c] = (int)inv[c].size();
     }
-    lv.ext = ar.put(ext);
+    lv.ext = arx.put(ext);
     lv.nstages = lesser ? 2 : 0;
     for (int k = 0; k < lv.nstages; ++k) {
-      lv.st[k].ops = ar.put(g[k]);
+      lv.st[k].ops = arx.put(g[k]);
       for (int c = 0; c < 6; ++c) {
-        lv.st[k].map[c] = ar.put(maps[k][c]);
+        lv.st[k].map[c] = arx.put(maps[k][c]);
         lv.st[k].nmap[c] = (int)maps[k][c].size();
       }
     }
-    scratch_elems = escr;
-    levels.push_back(lv);
+    finish_tc(lv, tcq, lv.nstages, off, arx, dry, need);
+    lvx.push_back(lv);
+  };
+
+  auto build_all = [&](Arena& arx, std::vector<Level>& lvx, bool dry, int64_t& need) {
+    lvx.clear();
+    for (const auto& lv : p.up_levels) elim_level(lv, arx, lvx, dry, need);
+    h->n_up = (int)p.up_levels.size();
+    for (const auto& lv : p.dn_levels) elim_level(lv, arx, lvx, dry, need);
+    h->n_dn = (int)p.dn_levels.size();
+    leaf_level(arx, lvx, dry, need);
+  };
+  {
+    int64_t need = 0;
+    Arena a0;
+    std::vector<Level> l0;
+    Bounds* const bc_real = bc;  // the dry build's pointers use a provisional escr
+    bc = nullptr;
+    build_all(a0, l0, true, need);
+    bc = bc_real;
+    escr = (std::max(escr, need) + 63) & ~int64_t(63);
   }
+  int64_t need = 0;
+  build_all(ar_out, levels_out, false, need);
+  scratch_elems = escr;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -646,10 +813,15 @@ int ensure_workspace(find_handle* h, int batch, bool lesser) {
   bc.s_lo = ws + L.scratch;
   bc.s_hi = ws + L.scratch + (size_t)se * batch * sizeof(cplx);
   bc.s_stride = se * (int64_t)sizeof(cplx);
-  build_tables(h, ws, L, batch, lesser, real, h->levels, se, &bc);
+  int map_err = 0;
+  build_tables(h, ws, L, batch, lesser, real, h->levels, se, &bc, &map_err);
   if (!bc.err.empty()) {
     release(h);
     return fail(h, FIND_EINVAL, "internal table check failed: " + bc.err);
+  }
+  if (map_err) {
+    release(h);
+    return fail(h, FIND_ECUDA, "tensor map encoding of the digit planes failed");
   }
   const findgb::Plan& p = h->plan;
   e = cudaMemcpy(ws + L.V, h->V.data(), h->V.size() * 8, cudaMemcpyHostToDevice);
@@ -687,10 +859,11 @@ const T* at(const find_handle* h, size_t off) {
   return reinterpret_cast<const T*>(h->ws + h->lay.meta + off);
 }
 
-const int kClasses = 15;
-const char* kClassNames[kClasses] = {"lead",    "assemble", "invert",   "lu",       "trsm",
-                                     "zgemm32", "zgemm64",  "extract",  "cgemm32",  "cgemm64",
-                                     "ffgemm32", "ffgemm64", "fftrsm",  "fflu",     "ffinvert"};
+const int kClasses = 17;
+const char* kClassNames[kClasses] = {"lead",     "assemble", "invert",  "lu",   "trsm",
+                                     "zgemm32",  "zgemm64",  "extract", "cgemm32", "cgemm64",
+                                     "ffgemm32", "ffgemm64", "fftrsm",  "fflu", "ffinvert",
+                                     "tcsplit",  "tcgemm"};
 // profiler class of each GEMM launch class 2 * arith + big
 const int kGemmClass[6] = {5, 6, 8, 9, 10, 11};
 
@@ -774,6 +947,16 @@ void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, boo
           findgb::launch_gemm(ops, at<int>(h, s.map[c]), s.nmap[c], c & 1, nb, st, c >> 1, e_off,
                               sym_mask);
         });
+    for (const TcChunk& c : s.tc) {
+      const findgb::TcOp* tops = at<findgb::TcOp>(h, c.ops);
+      timed(h, st, 15, 0.0, c.by * nb, [&] {
+        findgb::launch_tc_split(c.L, tops, at<int4>(h, c.sitems), c.nsitems, at<int4>(h, c.ritems),
+                                c.nritems, at<int4>(h, c.citems), c.ncitems, nb, st, e_off);
+      });
+      timed(h, st, 16, c.fl * nb, 0.0, [&] {
+        findgb::launch_tc_mma(c.L, tops, at<int>(h, c.tmap), c.ntiles, status, nb, st, e_off);
+      });
+    }
   }
   if (lv.leaf)
     timed(h, st, 7, 0.0, lv.by_ext * nb, [&] {
@@ -844,7 +1027,7 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
     }
   }
 
-  cudaError_t e = cudaMemsetAsync(status, 0x7f, sizeof(int), st);
+  cudaError_t e = cudaMemsetAsync(status, 0x7f, 2 * sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
   const int kNoError = 0x7f7f7f7f;
   if (lesser && dles && !dles_per_e) {
@@ -992,10 +1175,16 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
       if (e != cudaSuccess) return cuda_fail(h, e, "bond current copy-out");
     }
   }
-  int hs = kNoError;
-  e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  int hs2[2] = {kNoError, kNoError};
+  e = cudaMemcpyAsync(hs2, status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(h, e, "solve");
+  if (hs2[1] != kNoError) {
+    char buf[128];
+    std::snprintf(buf, sizeof buf, "a bounded wait of the tensor-core product ran out (role %d)", hs2[1]);
+    return fail(h, FIND_ETIMEOUT, buf);
+  }
+  const int hs = hs2[0];
   if (hs != kNoError) {
     char buf[128];
     std::snprintf(buf, sizeof buf, "exactly zero pivot at energy index %d", hs);
@@ -1061,6 +1250,13 @@ void run_level_static(find_handle* h, const StaticView& sv, const Level& lv,
     for (int c = 0; c < 6; ++c)
       findgb::launch_gemm(ops, reinterpret_cast<const int*>(meta(s.map[c])), s.nmap[c], c & 1, nb, st,
                           c >> 1, 0, sym_mask);
+    for (const TcChunk& c : s.tc) {
+      auto tops = reinterpret_cast<const findgb::TcOp*>(meta(c.ops));
+      findgb::launch_tc_split(c.L, tops, reinterpret_cast<const int4*>(meta(c.sitems)), c.nsitems,
+                              reinterpret_cast<const int4*>(meta(c.ritems)), c.nritems,
+                              reinterpret_cast<const int4*>(meta(c.citems)), c.ncitems, nb, st);
+      findgb::launch_tc_mma(c.L, tops, reinterpret_cast<const int*>(meta(c.tmap)), c.ntiles, status, nb, st);
+    }
   }
   if (lv.leaf)
     findgb::launch_extract(reinterpret_cast<const findgb::ExtractOp*>(meta(lv.ext)), lv.nops,
@@ -1109,9 +1305,11 @@ int solve_static(find_handle* h, const double* E, int nE, const double* sigL, co
     bc.s_lo = base + L.scratch;
     bc.s_hi = base + L.scratch + (size_t)se * batch * sizeof(cplx);
     bc.s_stride = se * (int64_t)sizeof(cplx);
-    build_tables(h, base, L, batch, false, real, lv, se, &bc);
+    int map_err = 0;
+    build_tables(h, base, L, batch, false, real, lv, se, &bc, &map_err);
     if (!bc.err.empty() || L.total > kStaticScratchBytes)
       return fail(h, FIND_EINVAL, "internal table check failed for the fixed scratch: " + bc.err);
+    if (map_err) return fail(h, FIND_ECUDA, "tensor map encoding of the digit planes failed");
     sv.base = base;
     sv.batch = batch;
     sv.lay = L;
@@ -1137,7 +1335,7 @@ int solve_static(find_handle* h, const double* E, int nE, const double* sigL, co
     if (e != cudaSuccess) return cuda_fail(h, e, "fixed scratch upload");
   }
   int* status = reinterpret_cast<int*>(base + L.status);
-  e = cudaMemsetAsync(status, 0x7f, sizeof(int), st);
+  e = cudaMemsetAsync(status, 0x7f, 2 * sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
   const int kNoError = 0x7f7f7f7f;
   cplx* dE = reinterpret_cast<cplx*>(base + L.E);
@@ -1185,10 +1383,16 @@ int solve_static(find_handle* h, const double* E, int nE, const double* sigL, co
       if (e != cudaSuccess) return cuda_fail(h, e, "diagG copy-out");
     }
   }
-  int hs = kNoError;
-  e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  int hs2[2] = {kNoError, kNoError};
+  e = cudaMemcpyAsync(hs2, status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(h, e, "solve");
+  if (hs2[1] != kNoError) {
+    char buf[128];
+    std::snprintf(buf, sizeof buf, "a bounded wait of the tensor-core product ran out (role %d)", hs2[1]);
+    return fail(h, FIND_ETIMEOUT, buf);
+  }
+  const int hs = hs2[0];
   if (hs != kNoError) {
     char buf[128];
     std::snprintf(buf, sizeof buf, "exactly zero pivot at energy index %d", hs);
@@ -1210,7 +1414,10 @@ int find_create(const find_desc* d, find_handle** out) {
   if (d->stencil != 5 && d->stencil != 9) return fail(nullptr, FIND_EINVAL, "stencil must be 5 or 9");
   if (d->max_batch < 0) return fail(nullptr, FIND_EINVAL, "max_batch < 0");
   if (d->gemm_small_max < 0) return fail(nullptr, FIND_EINVAL, "gemm_small_max < 0");
-  if (d->flags & ~(FIND_FLAG_FULL_U | FIND_FLAG_SYM_U | FIND_FLAG_GRAPH))
+  if (d->tc_slices < 0 || d->tc_slices > 12 || d->tc_slices_mixed < 0 || d->tc_slices_mixed > 12 ||
+      d->tc_min < 0)
+    return fail(nullptr, FIND_EINVAL, "tc_slices and tc_slices_mixed must be in [0, 12], tc_min >= 0");
+  if (d->flags & ~(FIND_FLAG_FULL_U | FIND_FLAG_SYM_U | FIND_FLAG_GRAPH | FIND_FLAG_NO_TC))
     return fail(nullptr, FIND_EINVAL, "unknown bit in flags");
   if (d->energy_group < 0 || d->sigma_c64_depth < 0)
     return fail(nullptr, FIND_EINVAL, "energy_group and sigma_c64_depth must be >= 0");
