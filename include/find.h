@@ -126,7 +126,19 @@ typedef struct {
    dominates).
      FIND_FLAG_FULL_U  both triangles on every path
      FIND_FLAG_SYM_U   one triangle on FIND_FP64 too (ignored with FULL_U)  */
-enum { FIND_FLAG_FULL_U = 1, FIND_FLAG_SYM_U = 2, FIND_FLAG_GRAPH = 4, FIND_FLAG_NO_TC = 8 };
+enum { FIND_FLAG_FULL_U = 1, FIND_FLAG_SYM_U = 2, FIND_FLAG_GRAPH = 4, FIND_FLAG_NO_TC = 8,
+       FIND_FLAG_LU = 16 };
+/* Symmetric elimination (Sec. 4.2).  With the closed-form leads A = A^T, and
+   FIND_FP64 eliminates every private inner set by LDL^T: M(S,S) is factored
+   as P M(S,S) P^T = T D T^T with the diagonal pivoting of Bunch and Kaufman
+   (1x1 and 2x2 blocks), W = T^-1 P M(S,B), and U = M(B,B) - W^T D^-1 W (Eq. 2
+   in symmetric form); L = M(B,S) M(S,S)^-1 for Eq. 7 comes from the same
+   factors.  Against the exact values on the 256x1024 mesh this form is tens
+   to hundreds of times more accurate than the LU form at the energies where
+   A is worst conditioned, and the factorisation takes half the LU's flops.
+   A call that passes Sigma_L or Sigma_R (not known to be symmetric) uses the
+   LU; switching between the two reallocates the workspace.  FIND_FLAG_LU
+   keeps the LU elimination for every call.  The mixed paths use the LU. */
 /* Tensor-core products.  The Schur-update products (Eq. 2, Eq. 7) and the
    leaf products G_K Sigma_K G_K^H run by default on the bf16 tensor cores
    (tcgen05) through an error-free digit-plane split of the complex128
@@ -263,7 +275,8 @@ int find_solve_diag_static(find_handle* h, const double* E, int nE,
  * solve's stream around every launch while profiling is on).  Kernel
  * classes: "lead", "assemble", "invert", "lu", "trsm", "zgemm32",
  * "zgemm64", "extract", "cgemm32", "cgemm64", "ffgemm32", "ffgemm64",
- * "fftrsm", "fflu", "ffinvert", "tcsplit", "tcgemm" (z: FP64, c: complex64,
+ * "fftrsm", "fflu", "ffinvert", "tcsplit", "tcgemm", "ldl" (ldl: the LDL^T
+ * factorisation, flops 8 s^3 / 6; z: FP64, c: complex64,
  * ff: float-float arithmetic; 32/64: tile size; tc: the tensor-core products,
  * split into digit planes, then multiplied).  flops are the algorithmic real
  * flops of the launches (GEMM: 8 m n k per op and energy; LU: 8 s^3 / 3;

@@ -48,7 +48,8 @@ class Find:
     def __init__(self, nx, ny, stencil=5, t=1.0, tp=0.0, V=None, onsite0=None, leaf=8,
                  device=0, max_batch=0, precision="fp64", fp64_top_levels=2, energy_group=0,
                  invert_smem=0, sigma_c64_depth=0, full_u=False, gemm_small_max=0, sym_u=False,
-                 graph=False, tensor_cores=True, tc_slices=0, tc_slices_mixed=0, tc_min=0):
+                 graph=False, tensor_cores=True, tc_slices=0, tc_slices_mixed=0, tc_min=0,
+                 ldl=True):
         _abi.load()
         self.nx, self.ny, self.stencil = int(nx), int(ny), int(stencil)
         self.n = self.nx * self.ny
@@ -67,7 +68,8 @@ class Find:
                            int(energy_group), int(invert_smem), int(sigma_c64_depth),
                            (_abi.FIND_FLAG_FULL_U if full_u else 0) | (_abi.FIND_FLAG_SYM_U if sym_u else 0)
                            | (_abi.FIND_FLAG_GRAPH if graph else 0)
-                           | (0 if tensor_cores else _abi.FIND_FLAG_NO_TC),
+                           | (0 if tensor_cores else _abi.FIND_FLAG_NO_TC)
+                           | (0 if ldl else _abi.FIND_FLAG_LU),
                            int(gemm_small_max), int(tc_slices), int(tc_slices_mixed), int(tc_min))
         self.handle = find_create(d)
         self.stats = find_plan_info(self.handle)

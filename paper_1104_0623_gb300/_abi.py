@@ -23,6 +23,7 @@ FIND_FLAG_FULL_U = 1
 FIND_FLAG_SYM_U = 2
 FIND_FLAG_GRAPH = 4
 FIND_FLAG_NO_TC = 8
+FIND_FLAG_LU = 16
 
 STATUS_NAMES = {0: "FIND_OK", 1: "FIND_EINVAL", 2: "FIND_ENOMEM", 3: "FIND_ESINGULAR",
                 4: "FIND_ETIMEOUT", 5: "FIND_ECUDA"}

@@ -652,6 +652,192 @@ __global__ void __launch_bounds__(kInvThreads, 2) k_lu_panel(const InvOp* __rest
   // TRSM, takes them as they are (k_trsm<true, true>)
 }
 
+// ---------------------------------------------------------------- LDL^T factorisation
+// Block-wide maximum of f(i) over i in [i0, i1) (first index on ties); every
+// thread gets (value, index); index -1 for an empty range.
+template <class Fn>
+__device__ __forceinline__ void block_argmax(int i0, int i1, Fn f, double* red_v, int* red_i,
+                                             double& best_out, int& idx_out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  double best = -1.0;
+  int bi = INT_MAX;
+  for (int i = i0 + tid; i < i1; i += blockDim.x) {
+    const double m = f(i);
+    if (m > best) { best = m; bi = i; }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ob = __shfl_down_sync(0xffffffffu, best, off);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  __syncthreads();  // red_v / red_i may still be read from a previous call
+  if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+  __syncthreads();
+  best = red_v[0];
+  bi = red_i[0];
+  for (int w = 1; w < nwarp; ++w)
+    if (red_v[w] > best || (red_v[w] == best && red_i[w] < bi)) { best = red_v[w]; bi = red_i[w]; }
+  best_out = best;
+  idx_out = bi == INT_MAX ? -1 : bi;
+}
+
+__device__ __forceinline__ double cabs1(cplx v) { return fabs(v.x) + fabs(v.y); }
+
+// Symmetric indefinite factorisation of the complex symmetric M(S,S) with
+// the diagonal pivoting of Bunch and Kaufman (Math. Comp. 31, 1977): at step k
+// with alpha = (1 + sqrt 17) / 8 and lambda the largest |.| below the
+// diagonal in column k (row r), take a 1x1 pivot a_kk when |a_kk| >= alpha
+// lambda, or when |a_kk| sigma >= alpha lambda^2 with sigma the largest
+// off-diagonal |.| in row/column r; else a 1x1 pivot a_rr when |a_rr| >=
+// alpha sigma; else the 2x2 pivot on {k, r}.  |.| is |re| + |im|.  Only the
+// lower triangle is read and updated (half the flops of the LU, Sec. 4.2).
+// On exit: P M P^T = T D T^T with T unit lower, stored below the diagonal
+// (zero at the sub-diagonal of each 2x2 block) and mirrored above it (the
+// forward sweep of k_trsm reads T^T there), ones on the diagonal; D in dv
+// (diagonal, then the 2x2 sub-diagonals); piv[j] the row and column
+// interchanged with j at its step (LU convention), kind[j] = 0 for a 1x1
+// block, 1 / 2 for the first / second index of a 2x2 block.  A pivot block
+// that is exactly singular records the energy in *status.
+__global__ void __launch_bounds__(kInvThreads) k_ldl(const InvOp* __restrict__ ops,
+                                                     int* __restrict__ status, int e_base,
+                                                     int e_off) {
+  const InvOp op = ops[blockIdx.x];
+  const int e = blockIdx.y + e_off;
+  const int s = op.s, ld = op.ld;
+  if (s == 0) return;
+  cplx* a = op.M + (int64_t)e * op.estride;
+  int* piv = op.piv + (int64_t)e * op.piv_estride;
+  int* kind = piv + s;
+  cplx* dv = op.dv + (int64_t)e * op.estride;
+  extern __shared__ double2 ldl_smem[];
+  cplx* c1 = ldl_smem;  // unscaled pivot columns
+  cplx* c2 = c1 + s;
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int sh_kp, sh_step;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+  auto A = [&](int i, int j) -> cplx& { return a[(int64_t)i * ld + j]; };
+  int k = 0;
+  while (k < s) {
+    double colmax;
+    int imax;
+    block_argmax(k + 1, s, [&](int i) { return cabs1(A(i, k)); }, red_v, red_i, colmax, imax);
+    const double absakk = cabs1(A(k, k));
+    int kp = k, step = 1;
+    if (colmax > 0.0 && absakk < alpha * colmax) {
+      double rm1, rm2;
+      int i1, i2;
+      block_argmax(k, imax, [&](int j) { return cabs1(A(imax, j)); }, red_v, red_i, rm1, i1);
+      block_argmax(imax + 1, s, [&](int j) { return cabs1(A(j, imax)); }, red_v, red_i, rm2, i2);
+      const double rowmax = fmax(rm1, rm2);
+      if (absakk * rowmax >= alpha * colmax * colmax) {
+        kp = k;
+      } else if (cabs1(A(imax, imax)) >= alpha * rowmax) {
+        kp = imax;
+      } else {
+        kp = imax;
+        step = 2;
+      }
+    }
+    if (tid == 0) { sh_kp = kp; sh_step = step; }
+    __syncthreads();
+    kp = sh_kp;
+    step = sh_step;
+    const int kk = k + step - 1;
+    if (kp != kk) {
+      // symmetric interchange of kk and kp on the lower triangle, and of the
+      // two rows of the columns already eliminated
+      if (tid == 0) {
+        const cplx t = A(kk, kk);
+        A(kk, kk) = A(kp, kp);
+        A(kp, kp) = t;
+      }
+      for (int j = kk + 1 + tid; j < kp; j += blockDim.x) {
+        const cplx t = A(j, kk);
+        A(j, kk) = A(kp, j);
+        A(kp, j) = t;
+      }
+      for (int i = kp + 1 + tid; i < s; i += blockDim.x) {
+        const cplx t = A(i, kk);
+        A(i, kk) = A(i, kp);
+        A(i, kp) = t;
+      }
+      for (int j = tid; j < kk; j += blockDim.x) {
+        const cplx t = A(kk, j);
+        A(kk, j) = A(kp, j);
+        A(kp, j) = t;
+      }
+    }
+    if (tid == 0) {
+      piv[k] = (step == 1) ? kp : k;
+      kind[k] = step == 1 ? 0 : 1;
+      if (step == 2) {
+        piv[k + 1] = kp;
+        kind[k + 1] = 2;
+      }
+    }
+    __syncthreads();
+    if (step == 1) {
+      const cplx d = A(k, k);
+      const bool zero = d.x == 0.0 && d.y == 0.0;
+      const cplx r = zero ? cmk(0, 0) : crecip(d);
+      if (tid == 0) {
+        dv[k] = d;
+        dv[s + k] = cmk(0, 0);
+        if (zero) atomicMin(status, e_base + e);
+      }
+      for (int i = k + 1 + tid; i < s; i += blockDim.x) {
+        const cplx c = A(i, k);
+        c1[i] = c;
+        A(i, k) = cmul(c, r);
+      }
+      __syncthreads();
+      // a_ij -= l_i c_j for k < j <= i, a warp per row
+      for (int i = k + 1 + warp; i < s; i += nwarp) {
+        const cplx li = A(i, k);
+        cplx* row = a + (int64_t)i * ld;
+        for (int j = k + 1 + lane; j <= i; j += 32) row[j] = cfms(li, c1[j], row[j]);
+      }
+    } else {
+      const cplx d11 = A(k, k), d21 = A(k + 1, k), d22 = A(k + 1, k + 1);
+      const cplx det = csub(cmul(d11, d22), cmul(d21, d21));
+      const bool zero = det.x == 0.0 && det.y == 0.0;
+      const cplx r = zero ? cmk(0, 0) : crecip(det);
+      const cplx e11 = cmul(d22, r), e22 = cmul(d11, r), e21 = cmk(-(cmul(d21, r).x), -(cmul(d21, r).y));
+      if (tid == 0) {
+        dv[k] = d11;
+        dv[k + 1] = d22;
+        dv[s + k] = d21;
+        dv[s + k + 1] = cmk(0, 0);
+        if (zero) atomicMin(status, e_base + e);
+      }
+      for (int i = k + 2 + tid; i < s; i += blockDim.x) {
+        const cplx x1 = A(i, k), x2 = A(i, k + 1);
+        c1[i] = x1;
+        c2[i] = x2;
+        A(i, k) = cfma(x2, e21, cmul(x1, e11));
+        A(i, k + 1) = cfma(x2, e22, cmul(x1, e21));
+      }
+      __syncthreads();
+      if (tid == 0) A(k + 1, k) = cmk(0, 0);  // T is the identity on the 2x2 block
+      for (int i = k + 2 + warp; i < s; i += nwarp) {
+        const cplx l1 = A(i, k), l2 = A(i, k + 1);
+        cplx* row = a + (int64_t)i * ld;
+        for (int j = k + 2 + lane; j <= i; j += 32) row[j] = cfms(l2, c2[j], cfms(l1, c1[j], row[j]));
+      }
+    }
+    __syncthreads();
+    k += step;
+  }
+  // unit diagonal, and T^T mirrored into the upper triangle
+  for (int idx = tid; idx < s * s; idx += blockDim.x) {
+    const int i = idx / s, j = idx % s;
+    if (i == j) A(i, i) = cmk(1.0, 0.0);
+    else if (j > i) A(i, j) = A(j, i);
+  }
+}
+
 // ---------------------------------------------------------------- grouped complex GEMM
 // Operands are complex128 in memory; CT is the arithmetic type: double2 (FP64
 // path) or float2 (complex64 arithmetic of the mixed path, operands rounded
@@ -754,10 +940,12 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4), sizeof(CT) == 16 ? (BM ==
           Bs[kk][j] = X::load((gk < K && gj < N) ? B[(int64_t)gk * ldb + gj] : cmk(0, 0), false);
         }
       } else {
+        // B stored n x k: op(B) = B^H (opb 1) or B^T (opb 2)
         for (int idx = threadIdx.x; idx < BK * BN; idx += NT) {
           int j = idx / BK, kk = idx % BK;
           int gk = k0 + kk, gj = n0 + j;
-          Bs[kk][j] = X::load((gk < K && gj < N) ? cconj(B[(int64_t)gj * ldb + gk]) : cmk(0, 0), false);
+          cplx v = (gk < K && gj < N) ? B[(int64_t)gj * ldb + gk] : cmk(0, 0);
+          Bs[kk][j] = X::load(opb == 1 ? cconj(v) : v, false);
         }
       }
       __syncthreads();
@@ -908,7 +1096,7 @@ __device__ __forceinline__ void rank_update(T* Y, const cplx* a, int ld, int s, 
   }
 }
 
-template <bool DF, bool FF>
+template <bool DF, bool FF, bool LDL>
 __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
                                               const int* __restrict__ tile_op, int rb, int e_off) {
   typedef TrsmArith<DF> X;
@@ -928,9 +1116,24 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
   __shared__ T pan[W][W];                           // the panel's block of the factor
   __shared__ T dgl[W];                              // reciprocals of the panel's diagonal
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (LDL) {
+    // the rows are taken in the pivoted order: entry j of M(B,S) P^T is entry
+    // perm[j] of M(B,S), perm the interchanges applied in order
+    if (tid == 0) {
+      for (int j = 0; j < s; ++j) perm[j] = j;
+      for (int j = 0; j < s; ++j) {
+        int p = piv[j];
+        if (p < j || p >= s) p = j;
+        const int t0 = perm[j];
+        perm[j] = perm[p];
+        perm[p] = t0;
+      }
+    }
+    __syncthreads();
+  }
   for (int idx = tid; idx < rows * s; idx += nt) {
     int r = idx / s, j = idx % s;
-    Y[r * s + j] = X::in(a[(int64_t)(s + r0 + r) * ld + j]);
+    Y[r * s + j] = X::in(a[(int64_t)(s + r0 + r) * ld + (LDL ? perm[j] : j)]);
   }
   // forward: Y U = B, panels of W columns left to right
   for (int j0 = 0; j0 < s; j0 += W) {
@@ -960,6 +1163,44 @@ __global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
     }
     __syncthreads();
     rank_update<X, FF>(Y, a, ld, s, rows, j0, w, j0 + w, s, tid, nt);  // the later columns
+    __syncthreads();
+  }
+  if (LDL) {
+    // W^T is the forward result; then W^T D^-1, with D's 1x1 and 2x2 blocks
+    const int* kind = piv + s;
+    const cplx* dv = op.dv + (int64_t)e * op.l_estride;
+    cplx* Wt = op.Wt + (int64_t)e * op.l_estride;
+    cplx* Yd = op.Yd + (int64_t)e * op.l_estride;
+    __syncthreads();
+    for (int idx = tid; idx < rows * s; idx += nt) {
+      const int r = idx / s, j = idx % s;
+      Wt[(int64_t)(r0 + r) * s + j] = X::out(Y[r * s + j]);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < rows * s; idx += nt) {
+      const int r = idx / s, j = idx % s;
+      const int kd = kind[j];
+      if (kd == 0) {
+        const cplx d = dv[j];
+        const bool z = d.x == 0.0 && d.y == 0.0;
+        Y[r * s + j] = X::mul(Y[r * s + j], z ? cmk(0, 0) : crecip(d));
+      } else if (kd == 1) {
+        const cplx d11 = dv[j], d22 = dv[j + 1], d21 = dv[s + j];
+        const cplx det = csub(cmul(d11, d22), cmul(d21, d21));
+        const bool z = det.x == 0.0 && det.y == 0.0;
+        const cplx rr = z ? cmk(0, 0) : crecip(det);
+        const cplx e11 = cmul(d22, rr), e22 = cmul(d11, rr);
+        const cplx e21 = cmk(-cmul(d21, rr).x, -cmul(d21, rr).y);
+        const cplx y1 = X::out(Y[r * s + j]), y2 = X::out(Y[r * s + j + 1]);
+        Y[r * s + j] = X::in(cfma(y2, e21, cmul(y1, e11)));
+        Y[r * s + j + 1] = X::in(cfma(y2, e22, cmul(y1, e21)));
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < rows * s; idx += nt) {
+      const int r = idx / s, j = idx % s;
+      Yd[(int64_t)(r0 + r) * s + j] = X::out(Y[r * s + j]);
+    }
     __syncthreads();
   }
   // backward: Z L = Y with L unit lower, panels of W columns right to left
@@ -1108,23 +1349,39 @@ int trsm_rows_per_block(int max_s) {
 }
 
 void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int max_s, int nE,
-                 cudaStream_t st, int df, int e_off, int ff_factors) {
+                 cudaStream_t st, int df, int e_off, int ff_factors, int ldl) {
   if (ntiles == 0 || max_s == 0) return;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_trsm<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
-    cudaFuncSetAttribute(k_trsm<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
-    cudaFuncSetAttribute(k_trsm<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
+    cudaFuncSetAttribute(k_trsm<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
+    cudaFuncSetAttribute(k_trsm<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
+    cudaFuncSetAttribute(k_trsm<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
+    cudaFuncSetAttribute(k_trsm<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
     attr_set = true;
   }
   size_t smem = (size_t)rb * max_s * sizeof(cplx) + (size_t)max_s * sizeof(int);
   dim3 grid(ntiles, nE);
-  if (df && ff_factors)
-    k_trsm<true, true><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
+  if (ldl)
+    k_trsm<false, false, true><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
+  else if (df && ff_factors)
+    k_trsm<true, true, false><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
   else if (df)
-    k_trsm<true, false><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
+    k_trsm<true, false, false><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
   else
-    k_trsm<false, false><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
+    k_trsm<false, false, false><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
+}
+
+void launch_ldl(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
+                cudaStream_t st, int e_off) {
+  if (nops == 0 || max_s <= 0) return;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_ldl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         2 * kMaxInvert * (int)sizeof(cplx));
+    attr_set = true;
+  }
+  dim3 grid(nops, nE);
+  k_ldl<<<grid, kInvThreads, 2 * (size_t)max_s * sizeof(cplx), st>>>(ops, status, e_base, e_off);
 }
 
 void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,

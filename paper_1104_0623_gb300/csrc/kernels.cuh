@@ -45,23 +45,34 @@ struct InvOp {
   int ld, s;
   int* piv;
   int64_t piv_estride;
+  cplx* dv;             // LDL^T only: D (2 s entries: diagonal, then the
+                        // sub-diagonal of the 2x2 blocks), stride estride
 };
 
 // L = M(B,S) M(S,S)^{-1} from the LU factors of M(S,S): rows r0..r0+rb of
 // M(B,S) per CTA; Y U = M(B,S), Z L = Y, L = Z P.
+//
+// LDL^T factors (k_ldl): P M(S,S) P^T = T D T^T.  Then L = M(B,S) P^T T^-T
+// D^-1 T^-1 P by the same two sweeps: the rows are first permuted by P^T,
+// the forward sweep with T^T gives W^T (rows of M(B,S) P^T T^-T), which is
+// stored together with W^T D^-1 (for U = M(B,B) - (W^T D^-1) W, the
+// symmetric form of Eq. 2); then the backward sweep with T and P.
 struct TrsmOp {
   const cplx* M;        // energy 0; M(S,S) holds the factors, M(B,S) the rows
   int64_t estride;
   int ld, s, b;
-  const int* piv;
+  const int* piv;       // LDL^T: piv[s] interchanges, then kind[s] block flags
   int64_t piv_estride;
   cplx* L;              // b x s, leading dimension s
-  int64_t l_estride;
+  int64_t l_estride;    // also the stride of dv, Wt and Yd
   int tile0;            // first row-block of this op in the launch
+  const cplx* dv;       // LDL^T: D as in InvOp::dv
+  cplx* Wt;             // LDL^T: W^T, b x s
+  cplx* Yd;             // LDL^T: W^T D^-1, b x s
 };
 
-// D = beta * C + alpha * A op(B) + alpha2 * A2 op(B2); op(B) = B (opb 0) or
-// B^H (opb 1, B stored n x k).  Every operand is row-major with its leading
+// D = beta * C + alpha * A op(B) + alpha2 * A2 op(B2); op(B) = B (opb 0),
+// B^H (opb 1, B stored n x k) or B^T (opb 2, B stored n x k).  Every operand is row-major with its leading
 // dimension and a per-energy stride.
 struct GemmOp {
   int m, n, k, k2;
@@ -104,11 +115,14 @@ void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_bas
 int invert_smem_max();
 void launch_lu(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
                cudaStream_t st, int e_off = 0, int df = 0);
+// Bunch-Kaufman LDL^T of the complex symmetric M(S,S) (Sec. 4.2), FP64
+void launch_ldl(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
+                cudaStream_t st, int e_off = 0);
 // df = 1: the row block is carried in float-float arithmetic; ff_factors = 1:
 // the LU factors of M(S,S) are float-float words (the float-float LU leaves
 // them so), else complex128
 void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int max_s, int nE,
-                 cudaStream_t st, int df = 0, int e_off = 0, int ff_factors = 0);
+                 cudaStream_t st, int df = 0, int e_off = 0, int ff_factors = 0, int ldl = 0);
 int trsm_rows_per_block(int max_s);
 // fp32 = 1: complex64 arithmetic on complex128 operands (mixed path);
 // fp32 = 2: float-float arithmetic (about 48 significant bits)

@@ -120,6 +120,7 @@ struct Layout {  // byte offsets inside the workspace
 // descriptor arena.
 struct StaticView {
   unsigned char* base = nullptr;
+  int ldl = -1;
   int batch = 0;
   Layout lay{};
   std::vector<Level> levels;
@@ -135,6 +136,8 @@ struct find_handle {
   std::string err;
   // current workspace
   int batch = 0, lesser = -1;
+  bool ldl = false;         // the current tables eliminate by LDL^T (else LU)
+  bool ldl_build = false;   // the mode build_tables lays out
   unsigned char* ws = nullptr;
   Layout lay{};
   std::vector<Level> levels;  // upward, then downward, then the leaf level
@@ -144,7 +147,7 @@ struct find_handle {
   bool prof = false;
   std::vector<cudaEvent_t> ev_free;
   std::vector<Pending> pending;
-  find_kernel_stat stats[17];
+  find_kernel_stat stats[18];
   // tables for the fixed device scratch
   StaticView sview;
   // streams and events of the concurrent energy groups of one pass
@@ -180,10 +183,13 @@ int cuda_fail(find_handle* h, cudaError_t e, const char* what) {
   return fail(h, e == cudaErrorMemoryAllocation ? FIND_ENOMEM : FIND_ECUDA, m);
 }
 
-// Per-energy scratch of one elimination: M [, Sigma_M], L [, T], pivots.
-int64_t op_slot_elems(const findgb::ElimOp& op, bool lesser) {
-  int64_t n = op.n, bs = (int64_t)op.b * op.s, piv = (op.s + 3) / 4;
-  return (lesser ? 2 * n * n + 2 * bs : n * n + bs) + piv;
+// Per-energy scratch of one elimination: M [, Sigma_M], L [, T], pivots; with
+// the LDL^T elimination also W^T and W^T D^-1 (b x s each), D (2 s) and the
+// block kinds (s ints after the pivots).
+int64_t op_slot_elems(const findgb::ElimOp& op, bool lesser, bool ldl) {
+  int64_t n = op.n, bs = (int64_t)op.b * op.s;
+  int64_t piv = ((ldl ? 2 : 1) * (int64_t)op.s + 3) / 4;
+  return (lesser ? 2 * n * n + 2 * bs : n * n + bs) + (ldl ? 2 * bs + 2 * (int64_t)op.s : 0) + piv;
 }
 
 int64_t leaf_slot_elems(const findgb::LeafOp& op, bool lesser) {
@@ -336,6 +342,8 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
   auto umat = [&](int id) { return id < 0 ? (cplx*)nullptr : U + p.mat_off[id] * batch; };
   auto rmat = [&](int id) { return (id < 0 || !R) ? (cplx*)nullptr : R + p.mat_off[id] * batch; };
   scratch_elems = 0;
+  // the LDL^T elimination (FP64 path, A = A^T) or the LU one
+  const bool ldl = h->ldl_build;
   const bool mixed = h->desc.precision == FIND_MIXED || h->desc.precision == FIND_MIXED_FF;
   const bool ff_all = h->desc.precision == FIND_MIXED_FF;
   // shared-memory inversion only on request: measured slower than the
@@ -368,12 +376,12 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
   int64_t escr = 0;
   for (const auto& lvops : p.up_levels) {
     int64_t t = 0;
-    for (const auto& op : lvops) t += op_slot_elems(op, lesser);
+    for (const auto& op : lvops) t += op_slot_elems(op, lesser, ldl);
     escr = std::max(escr, t);
   }
   for (const auto& lvops : p.dn_levels) {
     int64_t t = 0;
-    for (const auto& op : lvops) t += op_slot_elems(op, lesser);
+    for (const auto& op : lvops) t += op_slot_elems(op, lesser, ldl);
     escr = std::max(escr, t);
   }
   {
@@ -464,12 +472,16 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     lv.rb = findgb::trsm_rows_per_block(lv.max_s);
     int64_t off = 0;
     for (const auto& op : ops) {
-      const int64_t slot = op_slot_elems(op, lesser);
+      const int64_t slot = op_slot_elems(op, lesser, ldl);
       cplx* M = S0 + off;  // energy e at M + e * escr
       cplx* Sg = M + (int64_t)op.n * op.n;
       cplx* Lm = M + (lesser ? 2 : 1) * (int64_t)op.n * op.n;
       cplx* T = Lm + (int64_t)op.b * op.s;
-      int* piv = reinterpret_cast<int*>(Lm + (lesser ? 2 : 1) * (int64_t)op.b * op.s);
+      cplx* Wt = Lm + (lesser ? 2 : 1) * (int64_t)op.b * op.s;  // LDL^T only
+      cplx* Yd = Wt + (int64_t)op.b * op.s;
+      cplx* dv = Yd + (int64_t)op.b * op.s;
+      int* piv = reinterpret_cast<int*>(ldl ? dv + 2 * (int64_t)op.s
+                                            : Lm + (lesser ? 2 : 1) * (int64_t)op.b * op.s);
       off += slot;
       const int n = op.n, s = op.s, b = op.b;
       findgb::AsmOp a;
@@ -489,7 +501,8 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         if (a.u2) bc->block(a.u2, a.d2, a.d2, a.d2, (int64_t)a.d2 * a.d2, batch, "source U2");
         if (a.r1) bc->block(a.r1, a.d1, a.d1, a.d1, (int64_t)a.d1 * a.d1, batch, "source R1");
         if (a.r2) bc->block(a.r2, a.d2, a.d2, a.d2, (int64_t)a.d2 * a.d2, batch, "source R2");
-        if (s > 0) bc->block(reinterpret_cast<const cplx*>(piv), 1, (s + 3) / 4, (s + 3) / 4, escr, batch, "pivots");
+        const int pw = ((ldl ? 2 : 1) * s + 3) / 4;
+        if (s > 0) bc->block(reinterpret_cast<const cplx*>(piv), 1, pw, pw, escr, batch, "pivots");
         for (int q = 0; q < n && bc->err.empty(); ++q) {
           const findgb::Pos& pq = p.pos[op.pos + q];
           int d = pq.src == 1 ? a.d1 : pq.src == 2 ? a.d2 : 1;
@@ -503,7 +516,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       const Arith ua = below_top ? kFF : kFP64;
       if (s > 0) {
         const int lc = (ff_all && below_top) ? 1 : 0;
-        inv[lc].push_back(findgb::InvOp{M, escr, n, s, piv, escr * 4});
+        inv[lc].push_back(findgb::InvOp{M, escr, n, s, piv, escr * 4, ldl ? dv : nullptr});
         lv.inv_max[lc] = std::max(lv.inv_max[lc], s);
         lv.fl_inv[lc] += 8.0 * (double)s * s * s / 3.0;
         if (b > 0) {
@@ -512,6 +525,14 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
           t.M = M; t.estride = escr; t.ld = n; t.s = s; t.b = b;
           t.piv = piv; t.piv_estride = escr * 4;
           t.L = Lm; t.l_estride = escr;
+          t.dv = ldl ? dv : nullptr;
+          t.Wt = ldl ? Wt : nullptr;
+          t.Yd = ldl ? Yd : nullptr;
+          if (bc && ldl) {
+            bc->block(Wt, b, s, s, escr, batch, "trsm W^T");
+            bc->block(Yd, b, s, s, escr, batch, "trsm W^T D^-1");
+            bc->block(dv, 1, 2 * s, 2 * s, escr, batch, "ldl D");
+          }
           t.tile0 = (int)trs_map[tc].size();
           for (int r = 0; r < (b + lv.rb - 1) / lv.rb; ++r) trs_map[tc].push_back((int)trs.size());
           trs.push_back(t);
@@ -524,8 +545,14 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       // stage 0: U = M(B,B) - L M(S,B)                        (Eq. 2)
       findgb::GemmOp q = gemm0();
       q.m = b; q.n = b; q.k = s;
-      q.A = Lm; q.lda = s; q.sa = escr; q.alpha = -1.0;
-      q.B = M + s; q.ldb = n; q.sb = escr;
+      if (ldl && s > 0) {
+        // U = M(B,B) - (W^T D^-1) (W^T)^T, the symmetric form of Eq. 2 (Sec. 4.2)
+        q.A = Yd; q.lda = s; q.sa = escr; q.alpha = -1.0;
+        q.B = Wt; q.ldb = s; q.sb = escr; q.opb = 2;
+      } else {
+        q.A = Lm; q.lda = s; q.sa = escr; q.alpha = -1.0;
+        q.B = M + s; q.ldb = n; q.sb = escr;
+      }
       q.C = M + (int64_t)s * n + s; q.ldc = n; q.sc = escr; q.beta = 1.0;
       q.D = umat(op.dst); q.ldd = b; q.sd = (int64_t)b * b;
       q.sym = 1;  // U is complex symmetric when A is (Property 1)
@@ -751,7 +778,16 @@ Layout make_layout(const find_handle* h, int batch, bool lesser, int64_t scratch
   return L;
 }
 
-double workspace_bytes(find_handle* h, int batch, bool lesser, std::string* check_err = nullptr) {
+// The FP64 path eliminates by LDL^T (Sec. 4.2) unless FIND_FLAG_LU asks for
+// the LU; a call can use it only when A = A^T, i.e. with the closed-form lead
+// self-energies (Phi diag(sigma) Phi^T); a caller's Sigma takes the LU.
+bool default_ldl(const find_handle* h) {
+  return h->desc.precision == FIND_FP64 && !(h->desc.flags & FIND_FLAG_LU);
+}
+
+double workspace_bytes(find_handle* h, int batch, bool lesser, std::string* check_err = nullptr,
+                       int ldl = -1) {
+  h->ldl_build = ldl < 0 ? default_ldl(h) : ldl != 0;
   Arena ar;
   std::vector<Level> lv;
   int64_t se = 0;
@@ -790,9 +826,10 @@ void release(find_handle* h) {
   h->levels.clear();
 }
 
-int ensure_workspace(find_handle* h, int batch, bool lesser) {
-  if (h->ws && h->batch >= batch && (h->lesser == 1 || !lesser)) return FIND_OK;
+int ensure_workspace(find_handle* h, int batch, bool lesser, bool ldl) {
+  if (h->ws && h->batch >= batch && (h->lesser == 1 || !lesser) && h->ldl == ldl) return FIND_OK;
   release(h);
+  h->ldl_build = ldl;
   Arena ar;
   std::vector<Level> lv;
   int64_t se = 0;
@@ -806,6 +843,7 @@ int ensure_workspace(find_handle* h, int batch, bool lesser) {
   h->lay = L;
   h->batch = batch;
   h->lesser = lesser ? 1 : 0;
+  h->ldl = ldl;
   Arena real;
   Bounds bc;
   bc.lo = ws;
@@ -841,13 +879,14 @@ int ensure_workspace(find_handle* h, int batch, bool lesser) {
   return FIND_OK;
 }
 
-int choose_batch(find_handle* h, int nE, bool lesser) {
+int choose_batch(find_handle* h, int nE, bool lesser, bool ldl) {
   if (h->desc.max_batch > 0) return std::min(h->desc.max_batch, nE);
   size_t fr = 0, tot = 0;
-  if (h->ws && h->lesser >= (lesser ? 1 : 0)) return std::min(h->batch, nE);
+  if (h->ws && h->lesser >= (lesser ? 1 : 0) && h->ldl == ldl) return std::min(h->batch, nE);
+  if (h->ws && h->ldl != ldl) release(h);  // the other elimination's tables: free them first
   cudaMemGetInfo(&fr, &tot);
-  double one = workspace_bytes(h, 1, lesser);
-  double two = workspace_bytes(h, 2, lesser);
+  double one = workspace_bytes(h, 1, lesser, nullptr, ldl);
+  double two = workspace_bytes(h, 2, lesser, nullptr, ldl);
   double per = std::max(1.0, two - one);
   double budget = 0.70 * (double)fr - (one - per);
   int b = (int)std::floor(budget / per);
@@ -859,11 +898,11 @@ const T* at(const find_handle* h, size_t off) {
   return reinterpret_cast<const T*>(h->ws + h->lay.meta + off);
 }
 
-const int kClasses = 17;
+const int kClasses = 18;
 const char* kClassNames[kClasses] = {"lead",     "assemble", "invert",  "lu",   "trsm",
                                      "zgemm32",  "zgemm64",  "extract", "cgemm32", "cgemm64",
                                      "ffgemm32", "ffgemm64", "fftrsm",  "fflu", "ffinvert",
-                                     "tcsplit",  "tcgemm"};
+                                     "tcsplit",  "tcgemm", "ldl"};
 // profiler class of each GEMM launch class 2 * arith + big
 const int kGemmClass[6] = {5, 6, 8, 9, 10, 11};
 
@@ -926,16 +965,22 @@ void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, boo
         });
   } else {
     for (int c = 0; c < 2; ++c)
-      if (lv.ninv[c] > 0)
-        timed(h, st, c ? 13 : 3, lv.fl_inv[c] * nb, 0.0, [&] {
-          findgb::launch_lu(at<findgb::InvOp>(h, lv.inv[c]), lv.ninv[c], lv.inv_max[c], status, e_base,
-                            nb, st, e_off, c);
+      if (lv.ninv[c] > 0) {
+        const bool ldl = h->ldl && c == 0;  // LDL^T: half the flops of the LU
+        timed(h, st, ldl ? 17 : (c ? 13 : 3), lv.fl_inv[c] * (ldl ? 0.5 : 1.0) * nb, 0.0, [&] {
+          if (ldl)
+            findgb::launch_ldl(at<findgb::InvOp>(h, lv.inv[c]), lv.ninv[c], lv.inv_max[c], status, e_base,
+                               nb, st, e_off);
+          else
+            findgb::launch_lu(at<findgb::InvOp>(h, lv.inv[c]), lv.ninv[c], lv.inv_max[c], status, e_base,
+                              nb, st, e_off, c);
         });
+      }
     for (int c = 0; c < 2; ++c)
       if (lv.ntrsm[c] > 0)
         timed(h, st, c ? 12 : 4, lv.fl_trsm[c] * nb, 0.0, [&] {
           findgb::launch_trsm(at<findgb::TrsmOp>(h, lv.trsm), at<int>(h, lv.trsm_map[c]), lv.ntrsm[c],
-                              lv.rb, lv.max_s, nb, st, c, e_off, ff_factors(h, c));
+                              lv.rb, lv.max_s, nb, st, c, e_off, ff_factors(h, c), h->ldl && c == 0);
         });
   }
   for (int k = 0; k < lv.nstages; ++k) {
@@ -999,8 +1044,9 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const findgb::Plan& p = h->plan;
   const int64_t n = (int64_t)p.nx * p.ny, nx = p.nx;
-  int batch = choose_batch(h, nE, lesser);
-  int rc = ensure_workspace(h, batch, lesser);
+  const bool ldl = default_ldl(h) && !sigL && !sigR;
+  int batch = choose_batch(h, nE, lesser, ldl);
+  int rc = ensure_workspace(h, batch, lesser, ldl);
   if (rc != FIND_OK) return rc;
   batch = std::min(batch, h->batch);
   const Layout& L = h->lay;
@@ -1236,13 +1282,18 @@ void run_level_static(find_handle* h, const StaticView& sv, const Level& lv,
       findgb::launch_invert(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv[c])), lv.ninv[c],
                             lv.inv_max[c], status, e_base, nb, st, 0, c & 1, c >> 1);
   } else {
-    for (int c = 0; c < 2; ++c)
-      findgb::launch_lu(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv[c])), lv.ninv[c],
-                        lv.inv_max[c], status, e_base, nb, st, 0, c);
+    for (int c = 0; c < 2; ++c) {
+      if (sv.ldl == 1 && c == 0)
+        findgb::launch_ldl(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv[c])), lv.ninv[c],
+                           lv.inv_max[c], status, e_base, nb, st, 0);
+      else
+        findgb::launch_lu(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv[c])), lv.ninv[c],
+                          lv.inv_max[c], status, e_base, nb, st, 0, c);
+    }
     for (int c = 0; c < 2; ++c)
       findgb::launch_trsm(reinterpret_cast<const findgb::TrsmOp*>(meta(lv.trsm)),
                           reinterpret_cast<const int*>(meta(lv.trsm_map[c])), lv.ntrsm[c], lv.rb,
-                          lv.max_s, nb, st, c, 0, ff_factors(h, c));
+                          lv.max_s, nb, st, c, 0, ff_factors(h, c), sv.ldl == 1 && c == 0);
   }
   for (int k = 0; k < lv.nstages; ++k) {
     const Stage& s = lv.st[k];
@@ -1276,12 +1327,13 @@ int solve_static(find_handle* h, const double* E, int nE, const double* sigL, co
   cudaError_t e = static_scratch_address(h->desc.device, &base);
   if (e != cudaSuccess) return cuda_fail(h, e, "fixed scratch address");
   StaticView& sv = h->sview;
-  if (sv.base != base) {
+  const int ldl = (default_ldl(h) && !sigL && !sigR) ? 1 : 0;
+  if (sv.base != base || sv.ldl != ldl) {
     // size the largest energy batch that fits, then lay the tables out on it
     int batch = 0;
-    double need1 = workspace_bytes(h, 1, false);
+    double need1 = workspace_bytes(h, 1, false, nullptr, ldl);
     for (int b = 1; b <= 64; ++b) {
-      if (workspace_bytes(h, b, false) > (double)kStaticScratchBytes) break;
+      if (workspace_bytes(h, b, false, nullptr, ldl) > (double)kStaticScratchBytes) break;
       batch = b;
     }
     if (batch == 0) {
@@ -1295,6 +1347,7 @@ int solve_static(find_handle* h, const double* E, int nE, const double* sigL, co
     Arena sizing;
     std::vector<Level> lv;
     int64_t se = 0;
+    h->ldl_build = ldl != 0;
     Layout L0 = make_layout(h, batch, false, 0, 0);
     build_tables(h, nullptr, L0, batch, false, sizing, lv, se);
     Layout L = make_layout(h, batch, false, se, sizing.buf.size());
@@ -1311,6 +1364,7 @@ int solve_static(find_handle* h, const double* E, int nE, const double* sigL, co
       return fail(h, FIND_EINVAL, "internal table check failed for the fixed scratch: " + bc.err);
     if (map_err) return fail(h, FIND_ECUDA, "tensor map encoding of the digit planes failed");
     sv.base = base;
+    sv.ldl = ldl;
     sv.batch = batch;
     sv.lay = L;
     sv.levels = std::move(lv);
@@ -1417,7 +1471,7 @@ int find_create(const find_desc* d, find_handle** out) {
   if (d->tc_slices < 0 || d->tc_slices > 12 || d->tc_slices_mixed < 0 || d->tc_slices_mixed > 12 ||
       d->tc_min < 0)
     return fail(nullptr, FIND_EINVAL, "tc_slices and tc_slices_mixed must be in [0, 12], tc_min >= 0");
-  if (d->flags & ~(FIND_FLAG_FULL_U | FIND_FLAG_SYM_U | FIND_FLAG_GRAPH | FIND_FLAG_NO_TC))
+  if (d->flags & ~(FIND_FLAG_FULL_U | FIND_FLAG_SYM_U | FIND_FLAG_GRAPH | FIND_FLAG_NO_TC | FIND_FLAG_LU))
     return fail(nullptr, FIND_EINVAL, "unknown bit in flags");
   if (d->energy_group < 0 || d->sigma_c64_depth < 0)
     return fail(nullptr, FIND_EINVAL, "energy_group and sigma_c64_depth must be >= 0");

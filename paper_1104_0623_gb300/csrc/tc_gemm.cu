@@ -353,7 +353,7 @@ __device__ __forceinline__ void write_digits(cplx v, int ex, int P, int nsl, uns
 // Work items, one per CTA: (op, side, r0): rows r0 .. r0+7, a warp per row.
 // side 0: row i of A (all K, zero padding included); side 1: row j of the
 // planes of op(B), i.e. column j of op(B): this kernel writes the segments
-// that come from B^H operands (contiguous rows of the stored B) and every
+// that come from B^H and B^T operands (contiguous rows of the stored B) and every
 // zero; the segments from plain B operands are written by k_tc_split_cols.
 // Each lane takes K positions.
 __global__ void __launch_bounds__(256) k_tc_split_rows(const TcOp* __restrict__ ops,
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(256) k_tc_split_rows(const TcOp* __restrict__ 
           const cplx* B = part ? op.B2 + (int64_t)e * op.sb2 : op.B1 + (int64_t)e * op.sb1;
           const int ld = part ? op.ldb2 : op.ldb1;
           v = B[(int64_t)r * ld + kk];
-          v.y = -v.y;  // op(B) = B^H
+          if (opb == 1) v.y = -v.y;  // op(B) = B^H; opb 2: B^T
         }
       }
     }
