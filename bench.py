@@ -1,14 +1,20 @@
 #!/usr/bin/env python
 """Energy points per second of FIND (diag G, diag G< and bond currents) on the
-256x1024 9-point mesh (t' = 0.2 t, V ~ U[-1, 1] seed 1109, energies
-linspace(0.1, 7.9, 512) + 1e-6 i), FP64 path, one GB300 per rank.
+256x1024 9-point mesh (t' = 0.2 t, V ~ U[-1, 1] seed 1109, energies in
+[0.1, 7.9] + 1e-6 i), one GB300 per rank, on the mixed path by default:
+Schur and leaf products on the tensor cores (bf16 digit planes, 9 per
+operand), the other steps in float-float arithmetic, the top two tree levels
+in FP64.  --path fp64 times the FP64 path (LDL^T elimination, FP64 products).
 
 A step is one full FIND pass (lead self-energies, upward pass, downward pass,
 leaf extraction) over a batch of --batch energies.  Ranks take disjoint
-energies (weak scaling, no data-path collective).  Prints one JSON line.
+energies (weak scaling, no data-path collective).  Timed steps take distinct
+energies: the 512 grid points, then the midpoints between them.  Prints one
+JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
     python bench.py --impl reference ...   # the CPU oracle on the same workload
+    python bench.py --peaks                # FFMA / DFMA / DMMA peak probes only
 """
 
 import argparse
@@ -30,28 +36,38 @@ import workloads as W  # noqa: E402
 METRIC = "diag(G)+diag(G<) energy points/s at 256x1024"
 UNIT = "energy points/s"
 WORKLOAD = ("256x1024 mesh, 9-point stencil (t=1, t'=0.2), V~U[-1,1] seed 1109, "
-            "energies linspace(0.1,7.9,512)+1e-6i, outputs diag G, diag G<, bond currents")
-# Peaks of the arithmetic units, scaled by the SM clock sampled during the run:
-# FP64 (DFMA on the CUDA cores): nominal 1.25 TFLOP/s at the 2070 MHz maximum
-# SM clock; FP32: 128 lanes per SM x 152 SMs, one instruction per lane per
-# clock (an FFMA counts 2 flops).
-FP64_NOMINAL_TFLOPS = 1.25
-# FP64 tensor (DMMA m8n8k4) rate measured on this GPU by a throwaway probe at
-# 2070 MHz; DFMA on the CUDA cores measured 1.006 TFLOP/s
-FP64_DMMA_MEASURED_TFLOPS = 1.049
+            "energies in [0.1,7.9]+1e-6i (the 512-point grid, then its midpoints), outputs diag G, "
+            "diag G<, bond currents")
 SM_MAX_MHZ_NOMINAL = 2070.0
-N_SM = 152
 FP32_LANES = 128
-# FP32 instructions per float-float complex multiply-add in the kernels:
-# four products of 12 instructions (1 mul, 3 fma, 8 add) and two 3-add
-# renormalisations.
-FF_INST_PER_CMAC = 54
-# DRAM traffic per launch of the dominant kernel class (dram__bytes_read.sum +
-# dram__bytes_write.sum).  Empty: the launches of a class differ by tree level
-# and the ncu captures (profiles/) are of the 128x512 profiling case, where the
-# float-float GEMM moved 0.29-0.47 GB per 3.2-3.5 ms launch (DRAM ~1 % busy);
-# no per-launch figure of the bench's launches is claimed.
+# FP32 instructions per complex multiply-add of the float-float kernels, from
+# their recipe: one float-float multiply-add (df_mac) is 1 mul + 3 fma for the
+# exact product and its cross terms + 6 adds of the two-sum + 2 adds folding
+# the low words = 12; a complex one is 4 of them = 48.  The GEMM renormalises
+# each accumulator (2 x 3 adds) once per 8-deep k block: 48 + 6/8 = 48.75;
+# the triangular solves, the LU and the Gauss-Jordan inversion renormalise
+# after every multiply-add: 48 + 6 = 54.
+FF_INST_PER_CMAC = {"ffgemm32": 48.75, "ffgemm64": 48.75, "fftrsm": 54.0, "fflu": 54.0,
+                    "ffinvert": 54.0}
+# digit-plane pairs per complex multiply-add of the tensor-core products on the
+# mixed path (9 planes: pairs with s + t <= 8) and real bf16 products per pair
+TC_PLANES_MIXED = 9
+TC_PAIRS = TC_PLANES_MIXED * (TC_PLANES_MIXED + 1) // 2
+TC_REAL_PER_PAIR = 4
+# DRAM traffic per launch of a kernel class at the bench configuration
+# (dram__bytes_read.sum + dram__bytes_write.sum), from the ncu captures
+# summarised in profiles/ (scaled as stated there); a class whose kernel
+# changed since its capture is left out.
 DOMINANT_TRAFFIC = {}
+
+
+def read_peaks():
+    """MEASURED_PEAKS.json (driver-written), or {}."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
 
 
 def measured_hbm_gbs():
@@ -85,10 +101,10 @@ def parse():
     ap.add_argument("--no-side-paths", action="store_true",
                     help="skip the one-step measurement of the other precision paths")
     ap.add_argument("--path", choices=["fp64", "mixed", "mixed_ff"], default="mixed_ff",
-                    help="fp64: every step in FP64; mixed: below the two top tree levels the "
-                         "U and Sigma updates, the solves for L and the leaf G< products in "
-                         "float-float, LU and leaf inversion FP64; mixed_ff: LU and leaf "
-                         "inversion in float-float too")
+                    help="fp64: every step in FP64 (LDL^T elimination); mixed: below the two "
+                         "top tree levels the Schur and leaf products on the tensor cores "
+                         "(9 digit planes) and the solves for L in float-float, LU and leaf "
+                         "inversion FP64; mixed_ff: LU and leaf inversion in float-float too")
     ap.add_argument("--serve-requests", type=int, default=6,
                     help="requests of the serving scenario (0 skips it)")
     ap.add_argument("--serve-lambdas", default="0.8",
@@ -96,6 +112,10 @@ def parse():
                          "of its measured capacity")
     ap.add_argument("--mesh", default="256x1024",
                     help="NXxNY of the 9-point mesh (smaller meshes only for profiling)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="only run the FFMA / DFMA / DMMA peak probes and print them")
+    ap.add_argument("--no-probe", action="store_true",
+                    help="skip the peak probes that give the FP64 and FP32 roofline denominators")
     return ap.parse_args()
 
 
@@ -162,33 +182,47 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(mesh, Es, gpu_solve=None):
-    """The oracle (O-find) as it stands on one energy point of the workload;
-    with gpu_solve, also the GPU path's normwise error at that energy."""
+def cpu_baseline(mesh, Es):
+    """The oracle (O-find) as it stands on one energy point of the workload."""
     from oracle import find as ofind, problem
     P = problem.MeshProblem.from_mesh(mesh)
     E = Es[len(Es) // 2]
     t = time.perf_counter()
-    rG, rGl, _, _ = ofind.find_outputs(P, E, leaf=8, bonds=False)
+    ofind.find_outputs(P, E, leaf=8, bonds=False)
     dt = time.perf_counter() - t
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    out = {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"1 of 512 energy points (E={E.real:.4f}+1e-6i), diag G + diag G<, "
-                     f"numpy/LAPACK FP64 on all {cores} host cores, {dt:.1f} s"}
-    accuracy = None
-    if gpu_solve is not None:
-        accuracy = accuracy_at([E.real, E.imag], mesh, gpu_solve, (rG, rGl))
-    cpu_baseline.ref = (rG, rGl)
-    return out, accuracy
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"1 of 512 energy points (E={E.real:.4f}+1e-6i), diag G + diag G<, "
+                      f"numpy/LAPACK FP64 on all {cores} host cores, {dt:.1f} s"}
 
 
-def accuracy_at(energy, mesh, gpu_solve, ref):
-    """Normwise max relative error of diag G and diag G< against the oracle."""
-    rG, rGl = ref
-    gG, gGl = gpu_solve(np.array([complex(energy[0], energy[1])]))
-    return {"energy": list(energy),
-            "max_rel_err_diagG": float(np.abs(gG[0] - rG).max() / np.abs(rG).max()),
-            "max_rel_err_diagGl": float(np.abs(gGl[0] - rGl).max() / np.abs(rGl).max())}
+def refined_batch():
+    """The 8 grid energies of tests/golden/c5_refined_samples.txt (values of
+    G and G< on sampled nodes from the extended-precision refinement of the
+    oracle) plus 24 more grid energies: one 32-energy batch."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from test_oracle_refined import read_golden
+    norms, rows = read_golden()
+    gold = sorted(norms)
+    rest = [i for i in np.linspace(3, 508, 40).astype(int) if i not in gold][:32 - len(gold)]
+    idx = np.array(sorted(gold + rest))
+    return idx, W.c5_energies()[idx], norms, rows
+
+
+def accuracy_vs_refined(idx, G, Gl, norms, rows):
+    """Per sampled energy: normwise error of diag G and diag G< on the sampled
+    nodes against the refined values (max over nodes / max over the mesh)."""
+    out = {}
+    for ei in sorted(norms):
+        k = int(np.nonzero(idx == ei)[0][0])
+        sel = [(n, g, gl) for e, n, g, gl in rows if e == ei]
+        nodes = np.array([x[0] for x in sel])
+        eG = np.abs(G[k][nodes] - np.array([x[1] for x in sel])).max() / norms[ei]["maxG"]
+        eGl = np.abs(Gl[k][nodes] - np.array([x[2] for x in sel])).max() / norms[ei]["maxGl"]
+        out[f"{norms[ei]['E'].real:.3f}"] = [float(eG), float(eGl)]
+    worst = max(max(v) for v in out.values())
+    return {"reference": "refined definition (tests/golden/c5_refined_samples.txt), 8 energies",
+            "max_rel_err": worst, "by_energy_G_Gl": out}
 
 
 def serving(device, n_requests, precision="mixed_ff", chunk=8, slots=4, lam_fracs=(0.8,)):
@@ -235,56 +269,90 @@ def serving(device, n_requests, precision="mixed_ff", chunk=8, slots=4, lam_frac
             "single_request_fp64_points_per_s": single}
 
 
-def kernel_roofline(p, f_sm):
+def kernel_roofline(p, f_sm, n_sm, peaks):
     """Achieved rate of one kernel class against the peak of the unit its
     arithmetic uses.  p: the library profiler's entry (algorithmic real flops,
     8 per complex multiply-add, and summed event time)."""
     t = p["ms"] / 1e3
-    if p["name"].startswith("ff"):
-        # float-float: FP32 instructions issued per second
-        achieved = p["flops"] / 8.0 * FF_INST_PER_CMAC / t / 1e12
-        peak = FP32_LANES * N_SM * f_sm * 1e6 / 1e12
-        src = (f"float-float: {FF_INST_PER_CMAC} FP32 instructions per complex multiply-add; "
-               f"peak {FP32_LANES} lanes x {N_SM} SMs x {f_sm:.0f} MHz, FP32 instructions/s")
-    elif p["name"].startswith("c"):
-        achieved = p["flops"] / t / 1e12
-        peak = 2 * FP32_LANES * N_SM * f_sm * 1e6 / 1e12
-        src = f"complex64 FFMA: 2 x {FP32_LANES} lanes x {N_SM} SMs x {f_sm:.0f} MHz"
+    name = p["name"]
+    alg = p["flops"] / t / 1e12
+    out = {"kernel": name, "launches": p["launches"], "ms": p["ms"], "algorithmic_tflops": alg}
+    if name == "tcgemm":
+        # every complex multiply-add is TC_PAIRS x 4 real bf16 products
+        achieved = alg * TC_PAIRS * TC_REAL_PER_PAIR / 4.0
+        peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        out.update(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s",
+                   frac=achieved / peak if peak else None,
+                   peak_source="bf16 dense tensor peak of MEASURED_PEAKS.json (sustained, of measured); "
+                               f"achieved = algorithmic x {TC_PAIRS} plane pairs x 4 real / 4")
+    elif name in FF_INST_PER_CMAC:
+        ipc = FF_INST_PER_CMAC[name]
+        achieved = p["flops"] / 8.0 * ipc / t / 1e12
+        peak = FP32_LANES * n_sm * f_sm * 1e6 / 1e12
+        out.update(bound="alu", achieved=achieved, peak=peak, unit="T FP32 instructions/s",
+                   frac=achieved / peak,
+                   peak_source=f"float-float: {ipc} FP32 instructions per complex multiply-add; "
+                               f"issue peak {FP32_LANES} lanes x {n_sm} SMs x {f_sm:.0f} MHz")
+        ffma = peaks.get("ffma_tflops_probe")
+        out["frac_of_ffma_8flops"] = alg / ffma if ffma else None
     else:
-        achieved = p["flops"] / t / 1e12
-        peak = FP64_NOMINAL_TFLOPS * f_sm / SM_MAX_MHZ_NOMINAL
-        src = (f"FP64: nominal {FP64_NOMINAL_TFLOPS} TFLOP/s x sampled SM clock "
-               f"{f_sm:.0f}/{SM_MAX_MHZ_NOMINAL:.0f} MHz")
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "kernel": p["name"], "launches": p["launches"],
-            "ms": p["ms"], "peak_source": src}
+        peak = peaks.get("dmma_tflops_probe") or peaks.get("dfma_tflops_probe")
+        out.update(bound="alu", achieved=alg, peak=peak, unit="TFLOP/s",
+                   frac=alg / peak if peak else None,
+                   peak_source="FP64: the DMMA probe of this run (find_peak_probe kind 2)")
+    return out
 
 
-def side_path(F, mesh, Es, precision, B, device, rank, ws):
-    """One warm-up and one timed step of another precision path."""
+def side_path(F, mesh, precision, B, device):
+    """One warm-up and one timed step of another precision path, on the batch
+    that holds the 8 refined energies; with its accuracy against them."""
     import torch
-    from paper_1104_0623_gb300.shard import step_energies
+    idx, Es, norms, rows = refined_batch()
     f = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=B, precision=precision,
                          energy_group=B)
     dev = f"cuda:{device}"
     st = torch.cuda.current_stream(device)
-    E = [torch.tensor(step_energies(Es, k, rank, ws, B), dtype=torch.complex128, device=dev)
-         for k in range(2)]
+    E = torch.tensor(Es[:B], dtype=torch.complex128, device=dev)
     out = (torch.empty((B, mesh.n), dtype=torch.complex128, device=dev),
            torch.empty((B, mesh.n), dtype=torch.complex128, device=dev),
            torch.empty((B, f.n_bonds), dtype=torch.float64, device=dev))
-    f.solve_lesser(E[0], 1.0, 0.0, out=out, stream=st.cuda_stream)
+    f.solve_lesser(E, 1.0, 0.0, out=out, stream=st.cuda_stream)
     torch.cuda.synchronize(device)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st)
-    f.solve_lesser(E[1], 1.0, 0.0, out=out, stream=st.cuda_stream)
+    f.solve_lesser(E, 1.0, 0.0, out=out, stream=st.cuda_stream)
     e1.record(st)
     torch.cuda.synchronize(device)
     f.close()
     t = e0.elapsed_time(e1) / 1e3
+    acc = accuracy_vs_refined(idx, out[0].cpu().numpy(), out[1].cpu().numpy(), norms, rows)
     return {"value": B / t, "unit": UNIT, "ms_per_step": 1e3 * t, "energies_per_step": B,
-            "steps": 1, "warmup": 1}
+            "steps": 1, "warmup": 1}, acc
+
+
+def probe_peaks(F, device, seconds=1.5):
+    """FFMA, DFMA and DMMA rates of this GPU from find_peak_probe."""
+    out = {}
+    for kind, key in ((0, "ffma_tflops_probe"), (1, "dfma_tflops_probe"), (2, "dmma_tflops_probe")):
+        out[key] = F._abi.find_peak_probe(kind, seconds, device)
+    return out
+
+
+def bench_config(args, ws, B, extra=None):
+    """The `config` object of both arms (the same workload description)."""
+    cfg = {"workload": WORKLOAD if args.mesh == "256x1024" else f"{args.mesh} profiling case",
+           "energies_per_step": B, "leaf": 8, "path": args.path,
+           "parallelism": f"energy-sharded x{ws}, no data-path collective"}
+    cfg.update(extra or {})
+    return cfg
+
+
+DTYPE = {"mixed_ff": "c128 storage; Schur/leaf products bf16 tensor-core digit planes (9) with exact "
+                     "FP32 accumulation; LU, solves, inversion float-float (~48 bits); top 2 levels f64",
+         "mixed": "c128 storage; Schur/leaf products bf16 tensor-core digit planes (9); solves "
+                  "float-float; LU, inversion and top 2 levels f64",
+         "fp64": "f64 (LDL^T elimination, FP64 products on the CUDA cores)"}
 
 
 def run_reference(args):
@@ -292,24 +360,24 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import find as ofind, problem
-    mesh, Es = W.c5(), W.c5_energies()
+    mesh, Es = W.c5(), W.c5_bench_energies()
     P = problem.MeshProblem.from_mesh(mesh)
     for k in range(args.warmup):
-        ofind.find_outputs(P, Es[k], leaf=8, bonds=False)
+        ofind.find_outputs(P, Es[(args.steps + k) % len(Es)], leaf=8, bonds=False)
     t = time.perf_counter()
     for k in range(args.steps):
-        ofind.find_outputs(P, Es[args.warmup + k], leaf=8, bonds=False)
+        ofind.find_outputs(P, Es[k], leaf=8, bonds=False)
     dt = time.perf_counter() - t
     value = args.steps / dt
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic",
-           "config": {"workload": WORKLOAD, "energies_per_step": 1, "leaf": 8,
-                      "parallelism": "host cores (numpy/LAPACK threads)"},
+           "data": "synthetic", "config": bench_config(args, ws, args.batch),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": "1 energy point per step, diag G + diag G<"},
+                            "sample": f"1 energy point per step (the first {args.steps} timed "
+                                      f"energies of the GPU arm), diag G + diag G<, numpy/LAPACK "
+                                      f"FP64 on {cores} host cores"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -329,14 +397,25 @@ def main():
     import paper_1104_0623_gb300 as F
     from paper_1104_0623_gb300.shard import max_over_ranks, step_energies
 
-    mesh, Es = bench_mesh(args.mesh), W.c5_energies()
+    n_sm = torch.cuda.get_device_properties(device).multi_processor_count
+    peaks = read_peaks()
+    if args.peaks or not args.no_probe:
+        probe = probe_peaks(F, device)
+        if args.peaks:
+            print(json.dumps({"n_sm": n_sm, **probe}), flush=True)
+            return
+        peaks.update(probe)
+
+    mesh = bench_mesh(args.mesh)
+    Es = W.c5_bench_energies()
     B = args.batch
     f = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=B, precision=args.path,
                          energy_group=B)
     n, nb = mesh.n, f.n_bonds
     dev = f"cuda:{device}"
+    # timed step k takes batch k of the grid; warm-up steps take the batches after them
     E_dev = [torch.tensor(step_energies(Es, k, rank, ws, B), dtype=torch.complex128, device=dev)
-             for k in range(args.warmup + args.steps)]
+             for k in range(args.steps + args.warmup)]
     dG = torch.empty((B, n), dtype=torch.complex128, device=dev)
     dGl = torch.empty((B, n), dtype=torch.complex128, device=dev)
     J = torch.empty((B, nb), dtype=torch.float64, device=dev)
@@ -346,7 +425,7 @@ def main():
         f.solve_lesser(E_dev[k], 1.0, 0.0, out=(dG, dGl, J), stream=stream.cuda_stream)
 
     for k in range(args.warmup):
-        step(k)
+        step(args.steps + k)
     torch.cuda.synchronize(device)
 
     def barrier():
@@ -362,7 +441,7 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(args.steps):
-        step(args.warmup + k)
+        step(k)
     e1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -370,6 +449,7 @@ def main():
     f.profile(False)
     t = max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
     value = ws * args.steps * B / t
+    distinct = min(len(Es), ws * args.steps * B)
 
     # end-to-end through the C ABI with pinned host buffers (copies inside)
     e2e = None
@@ -388,23 +468,25 @@ def main():
         e2e = {"value": ws * args.steps * B / te, "unit": UNIT, "h2d_bytes_per_step": B * 16,
                "d2h_bytes_per_step": B * n * 16 * 2 + B * nb * 8}
 
-    # roofline of the dominant kernel class, against the unit its arithmetic runs on
     f_sm = clk.get("sm_mhz") or SM_MAX_MHZ_NOMINAL
-    compute = [p for p in prof if p["flops"] > 0]
+    compute = [p for p in prof if p["flops"] > 0 and p["launches"]]
     dom = max(compute, key=lambda p: p["ms"])
-    roofline = kernel_roofline(dom, f_sm)
+    roofline = kernel_roofline(dom, f_sm, n_sm, peaks)
     roofline["traffic"] = DOMINANT_TRAFFIC.get(dom["name"])
-    peak64 = FP64_NOMINAL_TFLOPS * f_sm / SM_MAX_MHZ_NOMINAL
-    path_flops = f.stats.flops_lesser * args.steps * B
-    path = {"achieved": path_flops / t / 1e12, "peak": peak64, "unit": "TFLOP/s",
-            "frac": path_flops / t / 1e12 / peak64,
-            "flops_per_energy": f.stats.flops_lesser,
-            "note": "algorithmic flops of the whole pass over the FP64 peak; on the mixed "
-                    "paths most of them run in float-float or complex64, so frac can exceed 1"}
-    kernels = {p["name"]: {"launches": p["launches"], "ms": round(p["ms"], 3),
-                           "share": p["ms"] / sum(q["ms"] for q in prof)} for p in prof if p["launches"]}
+    total_ms = sum(q["ms"] for q in prof)
+    kernels = {}
+    for p in prof:
+        if not p["launches"]:
+            continue
+        kernels[p["name"]] = {"launches": p["launches"], "ms": round(p["ms"], 3),
+                              "share": p["ms"] / total_ms}
+        if p["flops"] > 0:
+            r = kernel_roofline(p, f_sm, n_sm, peaks)
+            kernels[p["name"]].update({k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac",
+                                                          "algorithmic_tflops") if k in r})
     # the HBM-bound kernels (gather of M and Sigma_M, extraction of the
-    # outputs): algorithmic bytes moved / time, against the measured copy peak
+    # outputs, digit-plane split): algorithmic bytes moved / time, against the
+    # measured copy peak
     hbm_peak = measured_hbm_gbs()
     for p in prof:
         if p["launches"] and p["bytes"] > 0 and p["ms"] > 0:
@@ -412,46 +494,51 @@ def main():
             kernels[p["name"]]["achieved_gbs"] = gbs
             if hbm_peak:
                 kernels[p["name"]]["frac_of_measured_hbm"] = gbs / hbm_peak
+    path_flops = f.stats.flops_lesser * args.steps * B
+    path_tf = path_flops / t / 1e12
+    path = {"achieved": path_tf, "unit": "TFLOP/s", "flops_per_energy": f.stats.flops_lesser,
+            "frac_of_dmma_probe": path_tf / peaks["dmma_tflops_probe"] if peaks.get("dmma_tflops_probe") else None,
+            "frac_of_ffma_probe": path_tf / peaks["ffma_tflops_probe"] if peaks.get("ffma_tflops_probe") else None,
+            "frac_of_bf16_tensor": path_tf / peaks["bf16_tflops_sustained"] if peaks.get("bf16_tflops_sustained") else None,
+            "note": "algorithmic flops of the whole pass (the paper's dense-block count, 8 real flops "
+                    "per complex multiply-add) per second, against the FP64 DMMA rate, the FP32 FFMA "
+                    "rate (both probed on this GPU) and the measured bf16 tensor peak"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD if args.mesh == "256x1024" else f"{args.mesh} profiling case",
-                      "energies_per_step": B, "energy_groups_per_pass": 1, "leaf": 8, "path": args.path,
-                      "l2": f"inputs larger than L2: {f.workspace_bytes(B) / 2**30:.1f} GiB "
-                            f"resident U/R and scratch per step",
-                      "parallelism": f"energy-sharded x{ws}, no data-path collective"},
-           "clocks": clk, "gpu_launches": sum(p["launches"] for p in prof),
-           "roofline": roofline, "path_roofline": path, "kernels": kernels}
+           "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.path], "data": "synthetic",
+           "config": bench_config(args, ws, B, {
+               "energy_groups_per_pass": 1, "distinct_timed_energies": distinct,
+               "l2": f"inputs larger than L2: {f.workspace_bytes(B) / 2**30:.1f} GiB resident U/R "
+                     f"and scratch per step"}),
+           "clocks": clk, "n_sm": n_sm, "gpu_launches": sum(p["launches"] for p in prof),
+           "roofline": roofline, "path_roofline": path, "kernels": kernels,
+           "peaks_used": {k: v for k, v in peaks.items() if "tflops" in k or k == "hbm_gbs"}}
     if e2e:
         out["e2e"] = e2e
     f.close()
     paths = {args.path: {"value": value, "ms_per_step": 1e3 * t / args.steps}}
-    if not args.no_side_paths and args.mesh == "256x1024":
-        for other in ("fp64", "mixed", "mixed_ff"):
-            if other != args.path:
-                paths[other] = side_path(F, mesh, Es, other, B, device, rank, ws)
-    # each path's whole-pass algorithmic rate against the FP64 peak (nominal, at
-    # the sampled clock) and against the probe-measured DMMA rate
+    accuracy = {}
+    if args.mesh == "256x1024" and rank == 0:
+        idx, Eg, norms, rows = refined_batch()
+        g = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=B, precision=args.path,
+                             energy_group=B)
+        G, Gl, _ = g.solve_lesser(torch.tensor(Eg[:B], dtype=torch.complex128, device=dev), bonds=False)
+        g.close()
+        accuracy[args.path] = accuracy_vs_refined(idx, G.cpu().numpy(), Gl.cpu().numpy(), norms, rows)
+        if not args.no_side_paths:
+            for other in ("fp64", "mixed", "mixed_ff"):
+                if other != args.path:
+                    paths[other], accuracy[other] = side_path(F, mesh, other, B, device)
     for v in paths.values():
         tf = f.stats.flops_lesser * v["value"] / 1e12
         v["algorithmic_tflops"] = tf
-        v["frac_of_fp64_peak"] = tf / peak64
-        v["frac_of_measured_fp64_dmma"] = tf / FP64_DMMA_MEASURED_TFLOPS
+        if peaks.get("dmma_tflops_probe"):
+            v["frac_of_dmma_probe"] = tf / peaks["dmma_tflops_probe"]
     out["paths"] = paths
+    if accuracy:
+        out["accuracy_vs_refined"] = accuracy
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.mesh == "256x1024":
-        def gpu_solver(precision):
-            def run(E):
-                g = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=1, precision=precision)
-                G, Gl, _ = g.solve_lesser(np.ascontiguousarray(E), bonds=False)
-                g.close()
-                return G, Gl
-            return run
-        out["cpu_baseline"], acc = cpu_baseline(mesh, Es, gpu_solver(args.path))
-        out["accuracy_vs_oracle"] = {args.path: acc}
-        for other in paths:
-            if other != args.path:
-                out["accuracy_vs_oracle"][other] = accuracy_at(acc["energy"], mesh, gpu_solver(other),
-                                                               cpu_baseline.ref)
+        out["cpu_baseline"] = cpu_baseline(mesh, W.c5_energies())
     if rank == 0 and ws == 1 and args.serve_requests > 0 and args.mesh == "256x1024":
         out["serving"] = serving(device, args.serve_requests,
                                  "mixed" if args.path == "fp64" else args.path,

@@ -298,6 +298,14 @@ int find_profile(find_handle* h, int enable);
  * the number of kernel classes. */
 int find_profile_read(find_handle* h, find_kernel_stat* out, int max, int* count);
 
+/* Peak probe of one arithmetic unit of `device` (not part of the method; the
+ * roofline denominators of the FP64 and float-float kernels): kind 0 = FP32
+ * FFMA, 1 = FP64 DFMA on the CUDA cores, 2 = FP64 DMMA (mma.sync m8n8k4).
+ * Runs independent FMA chains on 4 CTAs of 256 threads per SM for about
+ * `seconds` and writes the achieved TFLOP/s (2 flops per FMA) to *tflops.
+ * Synchronises the device; returns FIND_EINVAL for a bad kind or time. */
+int find_peak_probe(int kind, double seconds, int device, double* tflops);
+
 /* Free the plan and the device workspace.  NULL is accepted. */
 int find_destroy(find_handle* h);
 

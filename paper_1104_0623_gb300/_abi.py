@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "FIND_OK", 1: "FIND_EINVAL", 2: "FIND_ENOMEM", 3: "FIND_ESING
 
 EXPORTED = ["find_create", "find_plan_info", "find_workspace_bytes", "find_solve_diag",
             "find_solve_diag_static", "find_solve_lesser", "find_profile", "find_profile_read",
-            "find_destroy", "find_last_error"]
+            "find_destroy", "find_last_error", "find_peak_probe"]
 
 
 class find_desc(ctypes.Structure):
@@ -80,6 +80,7 @@ def load():
     lib.find_profile.argtypes = [vp, ip]
     lib.find_profile_read.argtypes = [vp, ctypes.POINTER(find_kernel_stat), ip, ctypes.POINTER(ip)]
     lib.find_destroy.argtypes = [vp]
+    lib.find_peak_probe.argtypes = [ip, dp, ip, ctypes.POINTER(dp)]
     lib.find_last_error.argtypes = [vp]
     lib.find_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -151,6 +152,13 @@ def find_profile_read(handle: int):
 
 def find_destroy(handle: int) -> None:
     _check(load().find_destroy(handle))
+
+
+def find_peak_probe(kind: int, seconds: float, device: int = 0) -> float:
+    """TFLOP/s of one arithmetic unit: 0 FFMA, 1 DFMA, 2 DMMA (see find.h)."""
+    t = ctypes.c_double()
+    _check(load().find_peak_probe(int(kind), float(seconds), int(device), ctypes.byref(t)))
+    return t.value
 
 
 def find_last_error(handle=None) -> str:

@@ -72,7 +72,9 @@ def test_refined_clean_wire_closed_form(E):
 
 
 def test_refinement_beats_the_plain_solve_on_an_ill_conditioned_system():
-    mpmath = pytest.importorskip("mpmath")
+    # a hard dependency: this is the only pin of the refinement itself, so a
+    # missing mpmath must fail the suite, not skip the pin
+    import mpmath
     # a closed 5x6 box (no leads) at E = an eigenvalue of H + 1e-7 i: A is
     # close to singular (cond ~ 1e8), so a plain double solve keeps only
     # about 8 digits
