@@ -9,16 +9,15 @@ The steps follow the paper in its own order and notation:
 * Eq. (13)  L = A(B,S) A(S,S)^{-1}
 * Eq. (2)   U = A(B,B) - L A(S,B)              (major update)
 * Eq. (7)   R = S(B,B) - L S(S,B) - S(B,S) L^H + L S(S,S) L^H   (Sigma update)
-* Procedure updateBoundaryNodes (upward pass, post-order): a leaf starts from
-  A(C,C) and Sigma(C,C); a merge assembles [U_C1 A(B1,B2); A(B2,B1) U_C2]
-  (original couplings off the diagonal blocks) and the same for Sigma with
-  R_C1, R_C2; the root is not eliminated.
-* Procedure updateAdjacentNodes (downward pass, pre-order): for C with parent
-  D and sibling D1, assemble over B_Dbar u B_D1 from (U_Dbar, U_D1) and
-  (R_Dbar, R_D1); when D is the root, Dbar is empty and the blocks of D1
-  alone are used (the paper's comment there names R_D1 for A; the reading
-  taken is U_Cbar from U_D1 and R_Cbar from R_D1).
-* Procedure computeG< and Sec. 3.2: for each leaf C,
+* Upward pass (Sec. 2.2, Sec. 3.1), children before parents: a leaf starts
+  from A(C,C) and Sigma(C,C); a merge assembles [U_C1 A(B1,B2); A(B2,B1) U_C2]
+  (original couplings off the diagonal blocks, Corollary 1) and the same for
+  Sigma with R_C1, R_C2; the root is not eliminated.
+* Downward pass (Sec. 2.2), parents before children: for C with parent D and
+  sibling D1, assemble over B_Dbar u B_D1 from (U_Dbar, U_D1) and (R_Dbar,
+  R_D1); when D is the root, Dbar is empty and the blocks of D1 alone are
+  used (the reading taken: U_Cbar from U_D1 and R_Cbar from R_D1).
+* Leaf extraction, Sec. 3.2: for each leaf C,
     Eq. (8)   G(C,C) = [A(C,C) - A(C,Bb) U_Cbar^{-1} A(Bb,C)]^{-1}
     Eq. (5)   G<(C,C) = U_nn^{-1} R_nn U_nn^{-H}, where U_nn, R_nn come from
               one more elimination (Eqs. 13, 2, 7) of Bb from the bordered
@@ -226,28 +225,49 @@ class FindOracle:
         elim = eliminate_symmetric if self.symmetric else eliminate
         return elim(M[np.ix_(perm, perm)], Sg[np.ix_(perm, perm)], s)
 
-    # -- Procedure updateBoundaryNodes
-    def update_boundary_nodes(self, c: int):
-        C = self.tree[c]
-        if C.children:
-            c1, c2 = C.children
-            self.update_boundary_nodes(c1)
-            self.update_boundary_nodes(c2)
-            nodes, M, Sg = self._merge(self.B[c1], self.B[c2], self.U[c1], self.U[c2],
-                                       self.R[c1], self.R[c2])
-        else:
-            nodes = C.nodes
-            M = self._a(nodes, nodes)
-            Sg = self._s(nodes, nodes)
-        if c == 0:
-            return
-        self.U[c], self.R[c] = self._eliminate_onto(nodes, M, Sg, self.B[c])
+    def _postorder(self):
+        """Cluster indices, children before parents (the root last)."""
+        order, stack = [], [(0, False)]
+        while stack:
+            c, expanded = stack.pop()
+            if expanded or not self.tree[c].children:
+                order.append(c)
+                continue
+            stack.append((c, True))
+            for ch in reversed(self.tree[c].children):
+                stack.append((ch, False))
+        return order
 
-    # -- Procedure updateAdjacentNodes
-    def update_adjacent_nodes(self, c: int):
-        C = self.tree[c]
-        if c != 0:
-            d = C.parent
+    def upward_pass(self):
+        """U_C and R_C for every cluster but the root (Sec. 2.2, Sec. 3.1),
+        children before parents.  A leaf's block is A(C,C) with Sigma<(C,C);
+        a parent's is the block over B_C1 u B_C2 assembled from its
+        children's U and R and the original couplings between the two sets
+        (Corollary 1); eliminating its private inner set S_C leaves U_C on
+        B_C (Eqs. 13, 2) and R_C (Eq. 7)."""
+        for c in self._postorder():
+            if c == 0:
+                continue
+            C = self.tree[c]
+            if C.children:
+                c1, c2 = C.children
+                nodes, M, Sg = self._merge(self.B[c1], self.B[c2], self.U[c1], self.U[c2],
+                                           self.R[c1], self.R[c2])
+            else:
+                nodes = C.nodes
+                M, Sg = self._a(nodes, nodes), self._s(nodes, nodes)
+            self.U[c], self.R[c] = self._eliminate_onto(nodes, M, Sg, self.B[c])
+
+    def downward_pass(self):
+        """U and R of every complement cluster Cbar (the mesh outside C,
+        eliminated onto B_Cbar), parents before children (Sec. 2.2): for C
+        with parent D and sibling D1 the block over B_Dbar u B_D1 comes from
+        (U_Dbar, U_D1) and (R_Dbar, R_D1) with the original couplings; for the
+        root's children Dbar is empty and the block is D1's own U and R."""
+        for c in reversed(self._postorder()):
+            if c == 0:
+                continue
+            d = self.tree[c].parent
             D = self.tree[d]
             d1 = D.children[1] if D.children[0] == c else D.children[0]
             if d == 0:
@@ -256,10 +276,8 @@ class FindOracle:
                 nodes, M, Sg = self._merge(self.Bbar[d], self.B[d1], self.Ubar[d], self.U[d1],
                                            self.Rbar[d], self.R[d1])
             self.Ubar[c], self.Rbar[c] = self._eliminate_onto(nodes, M, Sg, self.Bbar[c])
-        for ch in C.children:
-            self.update_adjacent_nodes(ch)
 
-    # -- leaf extraction (Procedure computeG<, Sec. 3.2)
+    # -- leaf extraction (Sec. 3.2, Eqs. 8-10)
     def leaf(self, c: int, bordered: bool):
         C = self.tree[c]
         nodes = C.nodes
@@ -288,13 +306,13 @@ class FindOracle:
         return G_CC, Gl_CC, np.concatenate([Bb, nodes]), GlK
 
     def run(self, H=None, bonds=None):
-        """Full computeG<: returns diag G, diag G<, and optionally the bond
+        """Both passes and every leaf: returns diag G, diag G<, and optionally the bond
         entries (G<_ji, G<_ij) for bonds i -> j, taken from the leaf holding
         i, plus the same pair taken from the leaf holding j (NaN when both
         ends share a leaf)."""
         n = self.nx * self.ny
-        self.update_boundary_nodes(0)
-        self.update_adjacent_nodes(0)
+        self.upward_pass()
+        self.downward_pass()
         diagG = np.zeros(n, np.complex128)
         diagGl = np.zeros(n, np.complex128)
         leaves = [k for k, c in enumerate(self.tree) if not c.children]
