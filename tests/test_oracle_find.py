@@ -129,6 +129,27 @@ def test_symmetry_preservation():
                 assert np.abs(R + R.conj().T).max() <= 1e-10 * np.abs(R).max()
 
 
+def test_sigma_update_vanishes_away_from_the_contacts():
+    # Sec. 4.3 (Sigma< sparsity): Sigma< lives on the contact columns only,
+    # so the upward R of a cluster with no contact node is exactly zero and
+    # the library skips its Eq. (7) products; every cluster touching a
+    # biased contact has R != 0, and every complement cluster too.
+    mesh = W.Mesh(12, 24, 9, 1.0, 0.2, -1.0, 1.0, 33)
+    P = problem.MeshProblem.from_mesh(mesh)
+    _, _, _, f = find.find_outputs(P, 2.1 + 1e-6j, fL=1.0, fR=0.4, leaf=4, bonds=False)
+    zero = nonzero = 0
+    for c, R in f.R.items():
+        C = f.tree[c]
+        if C.y0 > 0 and C.y1 < mesh.ny:
+            assert not np.any(R), c
+            zero += 1
+        else:
+            assert np.abs(R).max() > 0, c
+            nonzero += 1
+    assert zero > nonzero > 0
+    assert all(np.abs(R).max() > 0 for R in f.Rbar.values())
+
+
 def test_set_rules():
     # B_C lies in C, Bbar_C outside C; S_C = (B_C1 u B_C2) \ B_C contains no
     # node with a neighbour outside C; leaves tile the mesh.
