@@ -48,7 +48,7 @@ FP32_LANES = 128
 # the triangular solves, the LU and the Gauss-Jordan inversion renormalise
 # after every multiply-add: 48 + 6 = 54.
 FF_INST_PER_CMAC = {"ffgemm32": 48.75, "ffgemm64": 48.75, "fftrsm": 54.0, "fflu": 54.0,
-                    "ffinvert": 54.0}
+                    "ffinvert": 54.0, "ffldl": 54.0}
 # digit-plane pairs per complex multiply-add of the tensor-core products on the
 # mixed path (9 planes: pairs with s + t <= 8) and real bf16 products per pair
 TC_PLANES_MIXED = 9
@@ -114,6 +114,15 @@ def parse():
                     help="NXxNY of the 9-point mesh (smaller meshes only for profiling)")
     ap.add_argument("--peaks", action="store_true",
                     help="only run the FFMA / DFMA / DMMA peak probes and print them")
+    ap.add_argument("--serving-study", action="store_true",
+                    help="only the serving study: --serve-requests requests (c4 distribution) per "
+                         "arrival rate of --serve-lambdas, and single-request controls")
+    ap.add_argument("--control-requests", type=int, default=30,
+                    help="serving study: the first requests of the stream solved one at a time "
+                         "on the FP64 and on the mixed path (the controls)")
+    ap.add_argument("--crossover", default="",
+                    help="comma-separated N: time FIND (FP64, mixed) and the RGF baseline on square "
+                         "NxN 5-point meshes and print one JSON line per N")
     ap.add_argument("--no-probe", action="store_true",
                     help="skip the peak probes that give the FP64 and FP32 roofline denominators")
     return ap.parse_args()
@@ -269,6 +278,84 @@ def serving(device, n_requests, precision="mixed_ff", chunk=8, slots=4, lam_frac
             "single_request_fp64_points_per_s": single}
 
 
+def serving_study(device, n_requests, lam_fracs, n_control, precision="mixed_ff", chunk=8, slots=4):
+    """Continuous batching on the c4 stream: capacity from a closed loop of the
+    first n_control requests; then, per arrival rate (fraction of capacity),
+    n_requests Poisson arrivals served live; then the first n_control requests
+    one at a time (no batching, no overlap) on the FP64 path and on the same
+    mixed path, which separates the batching gain from the precision gain."""
+    import torch
+
+    import paper_1104_0623_gb300 as F
+    from paper_1104_0623_gb300.serve import GpuBackend, Request, Server, summarize
+    base = W.serving_stream(n_requests, rate_hz=1.0, seed=2011)
+    ctrl = base[:n_control]
+    closed = [Request(k, 0.0, r.mesh, r.energies) for k, r in enumerate(ctrl)]
+    srv = Server(GpuBackend(device, precision, chunk=chunk), slots=slots, chunk=chunk)
+    cap = summarize(srv.run(closed))
+    srv.close()
+    mean_pts = float(np.mean([len(r.energies) for r in base]))
+    by_lambda = []
+    for frac in lam_fracs:
+        lam = frac * cap["points_per_s"] / mean_pts
+        stream = W.serving_stream(n_requests, rate_hz=lam, seed=2011)
+        reqs = [Request(k, r.arrival_s, r.mesh, r.energies) for k, r in enumerate(stream)]
+        srv = Server(GpuBackend(device, precision, chunk=chunk), slots=slots, chunk=chunk)
+        sm = summarize(srv.run(reqs))
+        srv.close()
+        sm.update(lambda_frac_of_capacity=frac, lambda_req_per_s=lam, max_active=srv.max_active)
+        by_lambda.append(sm)
+        print(json.dumps({"partial": sm}), flush=True)
+    print(json.dumps({"partial": {"capacity_points_per_s": cap["points_per_s"]}}), flush=True)
+    controls = {}
+    torch.cuda.empty_cache()
+    for prec in ("fp64", precision):
+        torch.cuda.synchronize(device)
+        t = time.perf_counter()
+        for r in ctrl:
+            # the library sizes each handle's energy batch from the free memory
+            f = F.Find.from_mesh(r.mesh, leaf=8, device=device, precision=prec)
+            f.solve_lesser(np.ascontiguousarray(r.energies), bonds=False)
+            f.close()
+        dt = time.perf_counter() - t
+        controls[f"single_request_{prec}_points_per_s"] = sum(len(r.energies) for r in ctrl) / dt
+    return {"study": f"c4 stream (seed 2011): {n_requests} requests per arrival rate, {precision} path, "
+                     f"{slots} slots, {chunk}-energy chunks; capacity and controls on the first "
+                     f"{n_control} requests",
+            "mean_points_per_request": mean_pts, "capacity_points_per_s": cap["points_per_s"],
+            "by_lambda": by_lambda, **controls}
+
+
+def crossover(device, sizes, n_energies=16):
+    """FIND (FP64 with LDL^T, and the mixed path) against the recursive Green's
+    function baseline (FP64) on square N x N 5-point meshes (V ~ U[-0.5, 0.5]),
+    n_energies energies per call, the same GPU and kernels: energy points per
+    second of each, from the second of two calls (CUDA events)."""
+    import torch
+
+    import paper_1104_0623_gb300 as F
+    Es = torch.tensor(W.energy_grid(0.2, 3.8, n_energies), dtype=torch.complex128, device=f"cuda:{device}")
+    for N in sizes:
+        mesh = W.Mesh(N, N, 5, 1.0, 0.0, -0.5, 0.5, 1104 + N)
+        row = {"N": N, "energies": n_energies}
+        for name, prec in (("find_fp64", "fp64"), ("find_mixed_ff", "mixed_ff"), ("rgf_fp64", "fp64")):
+            f = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=n_energies, precision=prec,
+                                 energy_group=n_energies)
+            run = (lambda: f.solve_rgf(Es)) if name.startswith("rgf") else (lambda: f.solve_lesser(Es, bonds=False))
+            run()
+            st = torch.cuda.current_stream(device)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            run()
+            b.record(st)
+            torch.cuda.synchronize(device)
+            f.close()
+            row[name + "_points_per_s"] = n_energies / (a.elapsed_time(b) / 1e3)
+        row["rgf_time_over_find_fp64"] = row["find_fp64_points_per_s"] / row["rgf_fp64_points_per_s"]
+        print(json.dumps(row), flush=True)
+
+
 def kernel_roofline(p, f_sm, n_sm, peaks):
     """Achieved rate of one kernel class against the peak of the unit its
     arithmetic uses.  p: the library profiler's entry (algorithmic real flops,
@@ -397,6 +484,15 @@ def main():
     import paper_1104_0623_gb300 as F
     from paper_1104_0623_gb300.shard import max_over_ranks, step_energies
 
+    if args.crossover:
+        crossover(device, [int(x) for x in args.crossover.split(",")])
+        return
+    if args.serving_study:
+        out = serving_study(device, args.serve_requests,
+                            [float(x) for x in args.serve_lambdas.split(",") if x], args.control_requests,
+                            "mixed" if args.path == "fp64" else args.path)
+        print(json.dumps(out), flush=True)
+        return
     n_sm = torch.cuda.get_device_properties(device).multi_processor_count
     peaks = read_peaks()
     if args.peaks or not args.no_probe:

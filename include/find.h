@@ -127,7 +127,7 @@ typedef struct {
      FIND_FLAG_FULL_U  both triangles on every path
      FIND_FLAG_SYM_U   one triangle on FIND_FP64 too (ignored with FULL_U)  */
 enum { FIND_FLAG_FULL_U = 1, FIND_FLAG_SYM_U = 2, FIND_FLAG_GRAPH = 4, FIND_FLAG_NO_TC = 8,
-       FIND_FLAG_LU = 16 };
+       FIND_FLAG_LU = 16, FIND_FLAG_LDL = 32 };
 /* Symmetric elimination (Sec. 4.2).  With the closed-form leads A = A^T, and
    FIND_FP64 eliminates every private inner set by LDL^T: M(S,S) is factored
    as P M(S,S) P^T = T D T^T with the diagonal pivoting of Bunch and Kaufman
@@ -138,7 +138,14 @@ enum { FIND_FLAG_FULL_U = 1, FIND_FLAG_SYM_U = 2, FIND_FLAG_GRAPH = 4, FIND_FLAG
    A is worst conditioned, and the factorisation takes half the LU's flops.
    A call that passes Sigma_L or Sigma_R (not known to be symmetric) uses the
    LU; switching between the two reallocates the workspace.  FIND_FLAG_LU
-   keeps the LU elimination for every call.  The mixed paths use the LU. */
+   keeps the LU elimination for every call.  The mixed paths (bar 1e-5) take
+   the LU unless FIND_FLAG_LDL asks for the symmetric form, which makes them
+   about 20 times more accurate at the worst energy but, on the 256x1024
+   mesh, 26 % slower: their float-float LU is blocked in panels, the
+   Bunch-Kaufman factorisation is not.  With FIND_FLAG_LDL the factorisation
+   runs in the arithmetic of the path's LU (float-float below the top levels
+   on FIND_MIXED_FF) and the solves in float-float.  FIND_FLAG_LU wins when
+   both are set. */
 /* Tensor-core products.  The Schur-update products (Eq. 2, Eq. 7) and the
    leaf products G_K Sigma_K G_K^H run by default on the bf16 tensor cores
    (tcgen05) through an error-free digit-plane split of the complex128
@@ -260,7 +267,8 @@ int find_solve_lesser(find_handle* h, const double* E, int nE,
  *
  * Set-up: the first call on a device (with that device current) looks up the
  * array's device address once; make that first call before any stream
- * capture.
+ * capture.  Every call waits for its stream to finish its work before it
+ * returns (it reads back the status word), as find_solve_diag does.
  *
  * Sharing: all calls, from every handle, use the same array and leave their
  * data in it; each call uploads its own tables and clears its status word
@@ -271,15 +279,31 @@ int find_solve_diag_static(find_handle* h, const double* E, int nE,
                            const double* sigmaL, const double* sigmaR,
                            double* diagG, void* stream);
 
+/*
+ * diag(G) and diag(G<) by the recursive Green's function method (RGF), the
+ * O(Nx^3 Ny) method the paper compares FIND with (Sec. 1, Sec. 5): forward
+ * and backward sweeps over the Ny transport slices of Nx nodes, FP64, the
+ * energies of a pass in lockstep.  A baseline for the FIND/RGF crossover on
+ * this GPU, not a second solver: closed-form leads only, Sigma< = i (fL
+ * Gamma_L + fR Gamma_R) (no node-diagonal Sigma<, no bond currents).  Inputs
+ * and outputs as for find_solve_lesser (host or device); the handle keeps an
+ * RGF workspace of (2 Ny + 9) Nx^2 complex entries per energy of a pass
+ * beside the FIND one.  FIND_ESINGULAR if a slice block is exactly singular.
+ */
+int find_rgf_solve_lesser(find_handle* h, const double* E, int nE, double fL, double fR,
+                          double* diagG, double* diagGl, void* stream);
+
 /* Per-kernel timing of the handle's solves (CUDA events recorded on the
  * solve's stream around every launch while profiling is on).  Kernel
  * classes: "lead", "assemble", "invert", "lu", "trsm", "zgemm32",
  * "zgemm64", "extract", "cgemm32", "cgemm64", "ffgemm32", "ffgemm64",
- * "fftrsm", "fflu", "ffinvert", "tcsplit", "tcgemm", "ldl" (ldl: the LDL^T
- * factorisation, flops 8 s^3 / 6; z: FP64, c: complex64,
+ * "fftrsm", "fflu", "ffinvert", "tcsplit", "tcgemm", "ldl", "ffldl" (ldl:
+ * the LDL^T factorisation, flops 8 s^3 / 6; z: FP64, c: complex64,
  * ff: float-float arithmetic; 32/64: tile size; tc: the tensor-core products,
  * split into digit planes, then multiplied).  flops are the algorithmic real
- * flops of the launches (GEMM: 8 m n k per op and energy; LU: 8 s^3 / 3;
+ * flops of the launches (GEMM: 8 m n k per op and energy, only the tiles on
+ * or above the diagonal of a complex symmetric output computed on one
+ * triangle; LU: 8 s^3 / 3;
  * triangular solves: 8 s^2 b; leaf inversion: 8 n^3), bytes the algorithmic
  * DRAM bytes of the gather/extract kernels (blocks written plus source blocks
  * read) and of the plane split (operands read, planes written). */

@@ -19,12 +19,12 @@ import numpy as np
 
 from . import _abi
 from ._abi import (FIND_FP64, FIND_MIXED, FIND_MIXED_FF, FindError, find_create, find_destroy, find_last_error,  # noqa: F401
-                   find_plan_info, find_profile, find_profile_read, find_solve_diag,
-                   find_solve_lesser, find_workspace_bytes)
+                   find_plan_info, find_profile, find_profile_read, find_rgf_solve_lesser,
+                   find_solve_diag, find_solve_lesser, find_workspace_bytes)
 
 __all__ = ["Find", "FindError", "find_create", "find_destroy", "find_last_error", "find_plan_info",
-           "find_profile", "find_profile_read", "find_solve_diag", "find_solve_lesser",
-           "find_workspace_bytes"]
+           "find_profile", "find_profile_read", "find_rgf_solve_lesser", "find_solve_diag",
+           "find_solve_lesser", "find_workspace_bytes"]
 
 
 def _ptr(x, dtype_name):
@@ -49,7 +49,7 @@ class Find:
                  device=0, max_batch=0, precision="fp64", fp64_top_levels=2, energy_group=0,
                  invert_smem=0, sigma_c64_depth=0, full_u=False, gemm_small_max=0, sym_u=False,
                  graph=False, tensor_cores=True, tc_slices=0, tc_slices_mixed=0, tc_min=0,
-                 ldl=True):
+                 ldl=None):
         _abi.load()
         self.nx, self.ny, self.stencil = int(nx), int(ny), int(stencil)
         self.n = self.nx * self.ny
@@ -69,7 +69,7 @@ class Find:
                            (_abi.FIND_FLAG_FULL_U if full_u else 0) | (_abi.FIND_FLAG_SYM_U if sym_u else 0)
                            | (_abi.FIND_FLAG_GRAPH if graph else 0)
                            | (0 if tensor_cores else _abi.FIND_FLAG_NO_TC)
-                           | (0 if ldl else _abi.FIND_FLAG_LU),
+                           | {None: 0, True: _abi.FIND_FLAG_LDL, False: _abi.FIND_FLAG_LU}[ldl],
                            int(gemm_small_max), int(tc_slices), int(tc_slices_mixed), int(tc_min))
         self.handle = find_create(d)
         self.stats = find_plan_info(self.handle)
@@ -136,6 +136,18 @@ class Find:
                           per_e, _ptr(dG, "complex128"), _ptr(dGl, "complex128"),
                           _ptr(J, "float64"), self._stream(stream, nE))
         return dG, dGl, J
+
+    def solve_rgf(self, E, fL=1.0, fR=0.0, stream=None, out=None):
+        """diag(G), diag(G<) by the recursive Green's function baseline (FP64)."""
+        nE = int(E.shape[0])
+        if out is None:
+            dG = self._out(E, (nE, self.n), np.complex128)
+            dGl = self._out(E, (nE, self.n), np.complex128)
+        else:
+            dG, dGl = out
+        find_rgf_solve_lesser(self.handle, _ptr(E, "complex128"), nE, fL, fR, _ptr(dG, "complex128"),
+                              _ptr(dGl, "complex128"), self._stream(stream, nE))
+        return dG, dGl
 
     def profile(self, enable=True):
         find_profile(self.handle, enable)

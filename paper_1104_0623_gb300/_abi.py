@@ -24,13 +24,14 @@ FIND_FLAG_SYM_U = 2
 FIND_FLAG_GRAPH = 4
 FIND_FLAG_NO_TC = 8
 FIND_FLAG_LU = 16
+FIND_FLAG_LDL = 32
 
 STATUS_NAMES = {0: "FIND_OK", 1: "FIND_EINVAL", 2: "FIND_ENOMEM", 3: "FIND_ESINGULAR",
                 4: "FIND_ETIMEOUT", 5: "FIND_ECUDA"}
 
 EXPORTED = ["find_create", "find_plan_info", "find_workspace_bytes", "find_solve_diag",
             "find_solve_diag_static", "find_solve_lesser", "find_profile", "find_profile_read",
-            "find_destroy", "find_last_error", "find_peak_probe"]
+            "find_destroy", "find_last_error", "find_peak_probe", "find_rgf_solve_lesser"]
 
 
 class find_desc(ctypes.Structure):
@@ -81,6 +82,7 @@ def load():
     lib.find_profile_read.argtypes = [vp, ctypes.POINTER(find_kernel_stat), ip, ctypes.POINTER(ip)]
     lib.find_destroy.argtypes = [vp]
     lib.find_peak_probe.argtypes = [ip, dp, ip, ctypes.POINTER(dp)]
+    lib.find_rgf_solve_lesser.argtypes = [vp, vp, ip, dp, dp, vp, vp, vp]
     lib.find_last_error.argtypes = [vp]
     lib.find_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -135,6 +137,12 @@ def find_solve_lesser(handle, E, nE, sigmaL, sigmaR, fL, fR, sigma_lesser_diag, 
     _check(load().find_solve_lesser(handle, E, nE, sigmaL, sigmaR, float(fL), float(fR),
                                     sigma_lesser_diag, int(diag_per_energy), diagG, diagGl,
                                     bond_current, stream), handle)
+
+
+def find_rgf_solve_lesser(handle, E, nE, fL, fR, diagG, diagGl, stream):
+    """diag G and diag G< by the recursive Green's function baseline (see find.h)."""
+    _check(load().find_rgf_solve_lesser(handle, E, nE, float(fL), float(fR), diagG, diagGl, stream),
+           handle)
 
 
 def find_profile(handle: int, enable: bool) -> None:

@@ -21,7 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfind_gb300.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "tc_gemm.cu", "runtime.cu", "plan.cpp", "peaks.cu"]
+SOURCES = ["kernels.cu", "tc_gemm.cu", "runtime.cu", "plan.cpp", "peaks.cu", "rgf.cu"]
 HEADERS = ["kernels.cuh", "plan.hpp"]
 
 

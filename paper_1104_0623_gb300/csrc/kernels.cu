@@ -225,37 +225,58 @@ __device__ __forceinline__ cplx s_orig(const DevProblem& P, int e, int i, int j)
 }
 
 // ---------------------------------------------------------------- assembly
-__global__ void __launch_bounds__(256) k_assemble(const AsmOp* __restrict__ ops,
+// One CTA per (row of an op, group of kAsmEnergies energies): the row's
+// position entries (which source block and index, or the original A and
+// Sigma<) do not depend on the energy, so they are read once per CTA and
+// reused for every energy of the group.
+constexpr int kAsmEnergies = 4;
+
+__global__ void __launch_bounds__(256, 3) k_assemble(const AsmOp* __restrict__ ops,
                                                   const int* __restrict__ row_op,
                                                   const Pos* __restrict__ pos, DevProblem P,
-                                                  int lesser, int e_off) {
-  const int r = blockIdx.x, e = blockIdx.y + e_off;
+                                                  int lesser, int e_off, int nE) {
+  const int r = blockIdx.x;
   const AsmOp& op = ops[row_op[r]];
   const int n = op.n;
   const int p = r - op.row0;
   const Pos pp = pos[op.pos + p];
-  cplx* Mrow = op.M + (int64_t)e * op.estride + (int64_t)p * n;
-  cplx* Srow = Mrow + (int64_t)n * n;
-  const cplx* U = nullptr;
-  const cplx* R = nullptr;
-  int d = 0;
-  if (pp.src == 1) {
-    d = op.d1;
-    U = op.u1 + (int64_t)e * d * d + (int64_t)pp.idx * d;
-    R = op.r1 ? op.r1 + (int64_t)e * d * d + (int64_t)pp.idx * d : nullptr;
-  } else if (pp.src == 2) {
-    d = op.d2;
-    U = op.u2 + (int64_t)e * d * d + (int64_t)pp.idx * d;
-    R = op.r2 ? op.r2 + (int64_t)e * d * d + (int64_t)pp.idx * d : nullptr;
-  }
+  const int e_lo = blockIdx.y * kAsmEnergies, e_hi = min(nE, e_lo + kAsmEnergies);
+  const int d = pp.src == 1 ? op.d1 : (pp.src == 2 ? op.d2 : 0);
+  // Sigma_M of an op whose nodes carry no Sigma< is zero and not read: skipped
+  const bool les = lesser && op.sig;
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
     const Pos pq = pos[op.pos + q];
     if (pp.src != 0 && pq.src == pp.src) {
-      Mrow[q] = U[pq.idx];
-      if (lesser) Srow[q] = R[pq.idx];
+      // the group's source entries first (independent loads in flight), then
+      // the stores
+      const cplx* U = pp.src == 1 ? op.u1 : op.u2;
+      const cplx* R = pp.src == 1 ? op.r1 : op.r2;
+      const int64_t off0 = (int64_t)pp.idx * d + pq.idx, dd = (int64_t)d * d;
+      cplx vu[kAsmEnergies], vr[kAsmEnergies];
+#pragma unroll
+      for (int u = 0; u < kAsmEnergies; ++u) {
+        const int e = e_lo + u + e_off;
+        if (e_lo + u < e_hi) {
+          vu[u] = U[e * dd + off0];
+          if (les) vr[u] = R ? R[e * dd + off0] : cmk(0, 0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kAsmEnergies; ++u) {
+        const int e = e_lo + u + e_off;
+        if (e_lo + u < e_hi) {
+          cplx* Mrow = op.M + (int64_t)e * op.estride + (int64_t)p * n;
+          Mrow[q] = vu[u];
+          if (les) Mrow[(int64_t)n * n + q] = vr[u];
+        }
+      }
     } else {
-      Mrow[q] = a_orig(P, e, pp.node, pq.node);
-      if (lesser) Srow[q] = s_orig(P, e, pp.node, pq.node);
+      for (int ee = e_lo; ee < e_hi; ++ee) {
+        const int e = ee + e_off;
+        cplx* Mrow = op.M + (int64_t)e * op.estride + (int64_t)p * n;
+        Mrow[q] = a_orig(P, e, pp.node, pq.node);
+        if (les) Mrow[(int64_t)n * n + q] = s_orig(P, e, pp.node, pq.node);
+      }
     }
   }
 }
@@ -691,6 +712,8 @@ __device__ __forceinline__ double cabs1(cplx v) { return fabs(v.x) + fabs(v.y); 
 // off-diagonal |.| in row/column r; else a 1x1 pivot a_rr when |a_rr| >=
 // alpha sigma; else the 2x2 pivot on {k, r}.  |.| is |re| + |im|.  Only the
 // lower triangle is read and updated (half the flops of the LU, Sec. 4.2).
+// FP64, or float-float (the block rewritten in place as float-float words
+// during the factorisation, like k_lu).
 // On exit: P M P^T = T D T^T with T unit lower, stored below the diagonal
 // (zero at the sub-diagonal of each 2x2 block) and mirrored above it (the
 // forward sweep of k_trsm reads T^T there), ones on the diagonal; D in dv
@@ -698,42 +721,55 @@ __device__ __forceinline__ double cabs1(cplx v) { return fabs(v.x) + fabs(v.y); 
 // interchanged with j at its step (LU convention), kind[j] = 0 for a 1x1
 // block, 1 / 2 for the first / second index of a 2x2 block.  A pivot block
 // that is exactly singular records the energy in *status.
+template <class T>
+__device__ __forceinline__ T neg_of(T v);
+template <>
+__device__ __forceinline__ cplx neg_of(cplx v) { return cmk(-v.x, -v.y); }
+template <>
+__device__ __forceinline__ float4 neg_of(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
+
+template <bool DF>
 __global__ void __launch_bounds__(kInvThreads) k_ldl(const InvOp* __restrict__ ops,
                                                      int* __restrict__ status, int e_base,
                                                      int e_off) {
+  typedef GA<DF> X;
+  typedef typename X::T T;
   const InvOp op = ops[blockIdx.x];
   const int e = blockIdx.y + e_off;
   const int s = op.s, ld = op.ld;
   if (s == 0) return;
-  cplx* a = op.M + (int64_t)e * op.estride;
+  cplx* g = op.M + (int64_t)e * op.estride;
   int* piv = op.piv + (int64_t)e * op.piv_estride;
   int* kind = piv + s;
   cplx* dv = op.dv + (int64_t)e * op.estride;
   extern __shared__ double2 ldl_smem[];
-  cplx* c1 = ldl_smem;  // unscaled pivot columns
-  cplx* c2 = c1 + s;
+  T* c1 = reinterpret_cast<T*>(ldl_smem);  // unscaled pivot columns
+  T* c2 = c1 + s;
   __shared__ double red_v[32];
   __shared__ int red_i[32];
   __shared__ int sh_kp, sh_step;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   const double alpha = (1.0 + sqrt(17.0)) / 8.0;
-  auto A = [&](int i, int j) -> cplx& { return a[(int64_t)i * ld + j]; };
+  to_work<X>(g, ld, s);
+  T* a = reinterpret_cast<T*>(g);
+  auto A = [&](int i, int j) -> T& { return a[(int64_t)i * ld + j]; };
+  auto mag = [&](int i, int j) { return (double)X::mag(A(i, j)); };
   int k = 0;
   while (k < s) {
     double colmax;
     int imax;
-    block_argmax(k + 1, s, [&](int i) { return cabs1(A(i, k)); }, red_v, red_i, colmax, imax);
-    const double absakk = cabs1(A(k, k));
+    block_argmax(k + 1, s, [&](int i) { return mag(i, k); }, red_v, red_i, colmax, imax);
+    const double absakk = mag(k, k);
     int kp = k, step = 1;
     if (colmax > 0.0 && absakk < alpha * colmax) {
       double rm1, rm2;
       int i1, i2;
-      block_argmax(k, imax, [&](int j) { return cabs1(A(imax, j)); }, red_v, red_i, rm1, i1);
-      block_argmax(imax + 1, s, [&](int j) { return cabs1(A(j, imax)); }, red_v, red_i, rm2, i2);
+      block_argmax(k, imax, [&](int j) { return mag(imax, j); }, red_v, red_i, rm1, i1);
+      block_argmax(imax + 1, s, [&](int j) { return mag(j, imax); }, red_v, red_i, rm2, i2);
       const double rowmax = fmax(rm1, rm2);
       if (absakk * rowmax >= alpha * colmax * colmax) {
         kp = k;
-      } else if (cabs1(A(imax, imax)) >= alpha * rowmax) {
+      } else if (mag(imax, imax) >= alpha * rowmax) {
         kp = imax;
       } else {
         kp = imax;
@@ -749,22 +785,22 @@ __global__ void __launch_bounds__(kInvThreads) k_ldl(const InvOp* __restrict__ o
       // symmetric interchange of kk and kp on the lower triangle, and of the
       // two rows of the columns already eliminated
       if (tid == 0) {
-        const cplx t = A(kk, kk);
+        const T t = A(kk, kk);
         A(kk, kk) = A(kp, kp);
         A(kp, kp) = t;
       }
       for (int j = kk + 1 + tid; j < kp; j += blockDim.x) {
-        const cplx t = A(j, kk);
+        const T t = A(j, kk);
         A(j, kk) = A(kp, j);
         A(kp, j) = t;
       }
       for (int i = kp + 1 + tid; i < s; i += blockDim.x) {
-        const cplx t = A(i, kk);
+        const T t = A(i, kk);
         A(i, kk) = A(i, kp);
         A(i, kp) = t;
       }
       for (int j = tid; j < kk; j += blockDim.x) {
-        const cplx t = A(kk, j);
+        const T t = A(kk, j);
         A(kk, j) = A(kp, j);
         A(kp, j) = t;
       }
@@ -779,32 +815,34 @@ __global__ void __launch_bounds__(kInvThreads) k_ldl(const InvOp* __restrict__ o
     }
     __syncthreads();
     if (step == 1) {
-      const cplx d = A(k, k);
+      // the pivot reciprocal in FP64 (Smith), split for float-float
+      const cplx d = X::to(A(k, k));
       const bool zero = d.x == 0.0 && d.y == 0.0;
-      const cplx r = zero ? cmk(0, 0) : crecip(d);
+      const T r = X::from(zero ? cmk(0, 0) : crecip(d));
       if (tid == 0) {
         dv[k] = d;
         dv[s + k] = cmk(0, 0);
         if (zero) atomicMin(status, e_base + e);
       }
       for (int i = k + 1 + tid; i < s; i += blockDim.x) {
-        const cplx c = A(i, k);
+        const T c = A(i, k);
         c1[i] = c;
-        A(i, k) = cmul(c, r);
+        A(i, k) = X::scale(c, r);
       }
       __syncthreads();
       // a_ij -= l_i c_j for k < j <= i, a warp per row
       for (int i = k + 1 + warp; i < s; i += nwarp) {
-        const cplx li = A(i, k);
-        cplx* row = a + (int64_t)i * ld;
-        for (int j = k + 1 + lane; j <= i; j += 32) row[j] = cfms(li, c1[j], row[j]);
+        const T li = A(i, k);
+        T* row = a + (int64_t)i * ld;
+        for (int j = k + 1 + lane; j <= i; j += 32) row[j] = X::fms(li, c1[j], row[j]);
       }
     } else {
-      const cplx d11 = A(k, k), d21 = A(k + 1, k), d22 = A(k + 1, k + 1);
+      const cplx d11 = X::to(A(k, k)), d21 = X::to(A(k + 1, k)), d22 = X::to(A(k + 1, k + 1));
       const cplx det = csub(cmul(d11, d22), cmul(d21, d21));
       const bool zero = det.x == 0.0 && det.y == 0.0;
       const cplx r = zero ? cmk(0, 0) : crecip(det);
-      const cplx e11 = cmul(d22, r), e22 = cmul(d11, r), e21 = cmk(-(cmul(d21, r).x), -(cmul(d21, r).y));
+      const T e11 = X::from(cmul(d22, r)), e22 = X::from(cmul(d11, r));
+      const T e21 = X::from(cmk(-(cmul(d21, r).x), -(cmul(d21, r).y)));
       if (tid == 0) {
         dv[k] = d11;
         dv[k + 1] = d22;
@@ -813,29 +851,33 @@ __global__ void __launch_bounds__(kInvThreads) k_ldl(const InvOp* __restrict__ o
         if (zero) atomicMin(status, e_base + e);
       }
       for (int i = k + 2 + tid; i < s; i += blockDim.x) {
-        const cplx x1 = A(i, k), x2 = A(i, k + 1);
+        const T x1 = A(i, k), x2 = A(i, k + 1);
         c1[i] = x1;
         c2[i] = x2;
-        A(i, k) = cfma(x2, e21, cmul(x1, e11));
-        A(i, k + 1) = cfma(x2, e22, cmul(x1, e21));
+        // l1 = x1 e11 + x2 e21, l2 = x1 e21 + x2 e22
+        A(i, k) = X::fms(x2, neg_of(e21), X::scale(x1, e11));
+        A(i, k + 1) = X::fms(x2, neg_of(e22), X::scale(x1, e21));
       }
       __syncthreads();
-      if (tid == 0) A(k + 1, k) = cmk(0, 0);  // T is the identity on the 2x2 block
+      if (tid == 0) A(k + 1, k) = X::zero();  // T is the identity on the 2x2 block
       for (int i = k + 2 + warp; i < s; i += nwarp) {
-        const cplx l1 = A(i, k), l2 = A(i, k + 1);
-        cplx* row = a + (int64_t)i * ld;
-        for (int j = k + 2 + lane; j <= i; j += 32) row[j] = cfms(l2, c2[j], cfms(l1, c1[j], row[j]));
+        const T l1 = A(i, k), l2 = A(i, k + 1);
+        T* row = a + (int64_t)i * ld;
+        for (int j = k + 2 + lane; j <= i; j += 32) row[j] = X::fms(l2, c2[j], X::fms(l1, c1[j], row[j]));
       }
     }
     __syncthreads();
     k += step;
   }
   // unit diagonal, and T^T mirrored into the upper triangle
+  const T one = X::from(cmk(1.0, 0.0));
   for (int idx = tid; idx < s * s; idx += blockDim.x) {
     const int i = idx / s, j = idx % s;
-    if (i == j) A(i, i) = cmk(1.0, 0.0);
+    if (i == j) A(i, i) = one;
     else if (j > i) A(i, j) = A(j, i);
   }
+  // the factors leave as complex128 (the solves split them when they read)
+  from_work<X>(g, ld, s);
 }
 
 // ---------------------------------------------------------------- grouped complex GEMM
@@ -1284,9 +1326,9 @@ void launch_lead_dense(const cplx* sig_modes, const double* phi, int nx, int nE,
 
 void launch_assemble(const AsmOp* ops, const int* row_op, int nrows, const Pos* pos,
                      const DevProblem& P, int lesser, int nE, cudaStream_t st, int e_off) {
-  if (nrows == 0) return;
-  dim3 grid(nrows, nE);
-  k_assemble<<<grid, 256, 0, st>>>(ops, row_op, pos, P, lesser, e_off);
+  if (nrows == 0 || nE == 0) return;
+  dim3 grid(nrows, (nE + kAsmEnergies - 1) / kAsmEnergies);
+  k_assemble<<<grid, 256, 0, st>>>(ops, row_op, pos, P, lesser, e_off, nE);
 }
 
 void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
@@ -1357,11 +1399,14 @@ void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int 
     cudaFuncSetAttribute(k_trsm<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
     cudaFuncSetAttribute(k_trsm<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
     cudaFuncSetAttribute(k_trsm<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
+    cudaFuncSetAttribute(k_trsm<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmSmem);
     attr_set = true;
   }
   size_t smem = (size_t)rb * max_s * sizeof(cplx) + (size_t)max_s * sizeof(int);
   dim3 grid(ntiles, nE);
-  if (ldl)
+  if (ldl && df)
+    k_trsm<true, false, true><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
+  else if (ldl)
     k_trsm<false, false, true><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
   else if (df && ff_factors)
     k_trsm<true, true, false><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
@@ -1372,16 +1417,21 @@ void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int 
 }
 
 void launch_ldl(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
-                cudaStream_t st, int e_off) {
+                cudaStream_t st, int e_off, int df) {
   if (nops == 0 || max_s <= 0) return;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_ldl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_ldl<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          2 * kMaxInvert * (int)sizeof(cplx));
+    cudaFuncSetAttribute(k_ldl<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         2 * kMaxInvert * (int)sizeof(float4));
     attr_set = true;
   }
   dim3 grid(nops, nE);
-  k_ldl<<<grid, kInvThreads, 2 * (size_t)max_s * sizeof(cplx), st>>>(ops, status, e_base, e_off);
+  if (df)
+    k_ldl<true><<<grid, kInvThreads, 2 * (size_t)max_s * sizeof(float4), st>>>(ops, status, e_base, e_off);
+  else
+    k_ldl<false><<<grid, kInvThreads, 2 * (size_t)max_s * sizeof(cplx), st>>>(ops, status, e_base, e_off);
 }
 
 void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,

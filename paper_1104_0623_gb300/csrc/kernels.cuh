@@ -30,10 +30,11 @@ struct DevProblem {
 struct AsmOp {
   int n, row0;
   int64_t pos;
-  const cplx* u1; const cplx* r1; int d1;  // source 1 (energy 0), stride d1*d1
+  const cplx* u1; const cplx* r1; int d1;  // source 1 (energy 0), stride d1*d1; r1 null: R = 0
   const cplx* u2; const cplx* r2; int d2;  // source 2
   cplx* M;                                 // energy 0; S_M = M + n*n
   int64_t estride;                         // per-energy stride of the op scratch
+  int sig;  // lesser passes: 1 writes Sigma_M; 0: Sigma_M is zero and nothing reads it
 };
 
 // In-place Gauss-Jordan inversion of the leading s x s block of M (ld); with
@@ -115,9 +116,10 @@ void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_bas
 int invert_smem_max();
 void launch_lu(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
                cudaStream_t st, int e_off = 0, int df = 0);
-// Bunch-Kaufman LDL^T of the complex symmetric M(S,S) (Sec. 4.2), FP64
+// Bunch-Kaufman LDL^T of the complex symmetric M(S,S) (Sec. 4.2); df = 1:
+// float-float arithmetic (the factors still leave as complex128)
 void launch_ldl(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
-                cudaStream_t st, int e_off = 0);
+                cudaStream_t st, int e_off = 0, int df = 0);
 // df = 1: the row block is carried in float-float arithmetic; ff_factors = 1:
 // the LU factors of M(S,S) are float-float words (the float-float LU leaves
 // them so), else complex128
@@ -134,6 +136,28 @@ void launch_extract(const ExtractOp* ops, int nops, const LeafBond* bonds, const
                     int64_t n_nodes, int64_t n_bonds, int nE, cudaStream_t st, int e_off = 0);
 
 constexpr int kMaxInvert = 2048;  // largest block the in-CTA inversion accepts
+
+// ---- recursive Green's function baseline (rgf.cu)
+struct RgfSlice {
+  int nx, ny, stencil;
+  double t, tp, onsite0;
+  const double* V;      // nx*ny onsite disorder
+  const cplx* E;        // energies of the pass
+  const cplx* sigL;     // [e][nx][nx]
+  const cplx* sigR;
+};
+// M = A_yy - C X C (X may be nullptr), per energy (strides in complex entries)
+void launch_rgf_block(const RgfSlice& s, int y, const cplx* X, int64_t xstride, cplx* M, int64_t mstride,
+                      int nE, cudaStream_t st);
+// W = sign C X, or C X C with sandwich = 1
+void launch_rgf_cprod(const RgfSlice& s, const cplx* X, int64_t xstride, cplx* W, int64_t wstride,
+                      double sign, int sandwich, int nE, cudaStream_t st);
+// out[x] (+)= (P Q^H)_xx; diagG[x] = diag_src[x][x] when diag_src is given
+void launch_rgf_diag(const RgfSlice& s, const cplx* P, const cplx* Q, int64_t stride, cplx* out,
+                     int64_t ostride, int accumulate, const cplx* diag_src, cplx* diagG, int nE,
+                     cudaStream_t st);
+// out = -f (sig - sig^H) per energy
+void launch_rgf_lesser(const cplx* sig, int nx, double f, cplx* out, int nE, cudaStream_t st);
 
 // ---- tensor-core products (tc_gemm.cu): D = beta C + a1 A1 op(B1) + a2 A2 op(B2)
 // computed from bf16 digit planes of the operands (see tc_gemm.cu).

@@ -86,6 +86,9 @@ struct Stage {
   size_t map[6] = {0, 0, 0, 0, 0, 0};  // arena offsets
   int nmap[6] = {0, 0, 0, 0, 0, 0};
   double fl[6] = {0, 0, 0, 0, 0, 0};   // algorithmic flops per energy of each class
+  // the same with complex-symmetric outputs computed on their upper tiles
+  // only (the mirrored launch): the flops those tiles execute
+  double fl_sym[6] = {0, 0, 0, 0, 0, 0};
   std::vector<TcChunk> tc;
 };
 
@@ -138,6 +141,9 @@ struct find_handle {
   int batch = 0, lesser = -1;
   bool ldl = false;         // the current tables eliminate by LDL^T (else LU)
   bool ldl_build = false;   // the mode build_tables lays out
+  // lesser tables that run every Sigma update (a caller's node-diagonal
+  // Sigma< reaches every cluster), and the mode build_tables lays out
+  bool sig_dense = false, sig_dense_build = false;
   unsigned char* ws = nullptr;
   Layout lay{};
   std::vector<Level> levels;  // upward, then downward, then the leaf level
@@ -147,7 +153,7 @@ struct find_handle {
   bool prof = false;
   std::vector<cudaEvent_t> ev_free;
   std::vector<Pending> pending;
-  find_kernel_stat stats[18];
+  find_kernel_stat stats[19];
   // tables for the fixed device scratch
   StaticView sview;
   // streams and events of the concurrent energy groups of one pass
@@ -167,6 +173,11 @@ struct find_handle {
   struct Graph { GraphKey key; cudaGraphExec_t exec; };
   std::vector<Graph> graphs;  // most recently used last
   cudaStream_t cap_stream = nullptr;
+  // the RGF baseline's own workspace (find_rgf_solve_lesser)
+  unsigned char* rgf_ws = nullptr;
+  int rgf_batch = 0;
+  size_t rgf_meta_bytes = 0;
+  size_t rgf_tab[3] = {0, 0, 0};  // GEMM ops, inversion ops, zero tile map (arena offsets)
 };
 
 namespace {
@@ -216,9 +227,17 @@ void add_gemm(findgb::GemmOp g, std::vector<findgb::GemmOp>& ops, std::vector<in
   if (g.m == 0 || g.n == 0) return;
   bool is_big = big_tiles(g.m, g.n, small_max, arith);
   const int cls = 2 * (int)arith + (is_big ? 1 : 0);
-  st->fl[cls] += 8.0 * g.m * g.n * (double)(g.k + (g.A2 ? g.k2 : 0));
+  const double kk = (double)(g.k + (g.A2 ? g.k2 : 0));
+  st->fl[cls] += 8.0 * g.m * g.n * kk;
   int bm = is_big ? 64 : 32;
   int tm = (g.m + bm - 1) / bm, tn = (g.n + bm - 1) / bm;
+  if (g.sym == 1) {
+    for (int i = 0; i < tm; ++i)
+      for (int j = i; j < tn; ++j)
+        st->fl_sym[cls] += 8.0 * std::min(bm, g.m - i * bm) * std::min(bm, g.n - j * bm) * kk;
+  } else {
+    st->fl_sym[cls] += 8.0 * g.m * g.n * kk;
+  }
   std::vector<int>& map = maps[cls];
   g.tile0 = (int)map.size();
   g.tiles_n = tn;
@@ -341,6 +360,18 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
   cplx* S0 = reinterpret_cast<cplx*>(base + L.scratch);
   auto umat = [&](int id) { return id < 0 ? (cplx*)nullptr : U + p.mat_off[id] * batch; };
   auto rmat = [&](int id) { return (id < 0 || !R) ? (cplx*)nullptr : R + p.mat_off[id] * batch; };
+  // Sigma< sparsity (Sec. 4.3): Sigma< is nonzero only on the contact columns
+  // y = 0 and y = Ny - 1 (and on a caller's node-diagonal term), so a cluster
+  // with no contact node has Sigma_M = 0 in its upward merge, and every term
+  // of Eq. (7) vanishes: R = 0.  Its T and R products are skipped, R is never
+  // stored, and the merges that read it take zeros.
+  std::vector<char> zsig(p.mat_dim.size(), 0);
+  if (lesser && !h->sig_dense_build)
+    for (size_t c = 0; c < p.cl.size(); ++c) {
+      const int id = p.up_mat[c];
+      if (id >= 0 && p.cl[c].y0 > 0 && p.cl[c].y1 < p.ny) zsig[id] = 1;
+    }
+  auto rsrc = [&](int id) { return (id >= 0 && zsig[id]) ? (cplx*)nullptr : rmat(id); };
   scratch_elems = 0;
   // the LDL^T elimination (FP64 path, A = A^T) or the LU one
   const bool ldl = h->ldl_build;
@@ -488,10 +519,12 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       a.n = n;
       a.row0 = lv.nrows;
       a.pos = op.pos;
-      a.u1 = umat(op.src1); a.r1 = rmat(op.src1); a.d1 = op.src1 < 0 ? 0 : p.mat_dim[op.src1];
-      a.u2 = umat(op.src2); a.r2 = rmat(op.src2); a.d2 = op.src2 < 0 ? 0 : p.mat_dim[op.src2];
+      a.u1 = umat(op.src1); a.r1 = rsrc(op.src1); a.d1 = op.src1 < 0 ? 0 : p.mat_dim[op.src1];
+      a.u2 = umat(op.src2); a.r2 = rsrc(op.src2); a.d2 = op.src2 < 0 ? 0 : p.mat_dim[op.src2];
       a.M = M;
       a.estride = escr;
+      const bool sig_op = lesser && !(op.dst >= 0 && zsig[op.dst]);
+      a.sig = sig_op ? 1 : 0;
       for (int r = 0; r < n; ++r) row_op.push_back((int)asmops.size());
       lv.nrows += n;
       asmops.push_back(a);
@@ -540,8 +573,9 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
           if (bc) bc->block(Lm, b, s, s, escr, batch, "trsm L");
         }
       }
-      lv.by_asm += 16.0 * ((lesser ? 2.0 : 1.0) * n * n +
-                           (lesser ? 2.0 : 1.0) * ((double)a.d1 * a.d1 + (double)a.d2 * a.d2));
+      lv.by_asm += 16.0 * ((sig_op ? 2.0 : 1.0) * n * n + (double)a.d1 * a.d1 + (double)a.d2 * a.d2 +
+                           (sig_op && a.r1 ? (double)a.d1 * a.d1 : 0.0) +
+                           (sig_op && a.r2 ? (double)a.d2 * a.d2 : 0.0));
       // stage 0: U = M(B,B) - L M(S,B)                        (Eq. 2)
       findgb::GemmOp q = gemm0();
       q.m = b; q.n = b; q.k = s;
@@ -560,7 +594,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       const int c64_from = h->desc.sigma_c64_depth;
       const Arith sa = !below_top ? kFP64
                        : ((c64_from > 0 && p.cl[op.cluster].depth >= c64_from) ? kC64 : kFF);
-      if (lesser) {
+      if (sig_op) {
         // stage 0: T = L Sigma(S,S) - Sigma(B,S)
         q = gemm0();
         q.m = b; q.n = s; q.k = s;
@@ -639,10 +673,11 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       a.n = n;
       a.row0 = lv.nrows;
       a.pos = op.pos;
-      a.u1 = umat(op.src); a.r1 = rmat(op.src); a.d1 = op.src < 0 ? 0 : p.mat_dim[op.src];
+      a.u1 = umat(op.src); a.r1 = rsrc(op.src); a.d1 = op.src < 0 ? 0 : p.mat_dim[op.src];
       a.u2 = nullptr; a.r2 = nullptr; a.d2 = 0;
       a.M = M;
       a.estride = escr;
+      a.sig = lesser ? 1 : 0;
       for (int r = 0; r < n; ++r) row_op.push_back((int)asmops.size());
       lv.nrows += n;
       asmops.push_back(a);
@@ -674,8 +709,14 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       lv.by_ext += 16.0 * (lesser ? 2.0 : 1.0) * op.c + (lesser ? 24.0 * op.nbond : 0.0);
       if (lesser) {
         // P = G_K(C, :) Sigma_K
+        // Sigma< sparsity (Sec. 4.3): a leaf with no contact node has
+        // Sigma_K = [R_Cbar 0; 0 0], so only the first nb columns of P are
+        // nonzero and both products run over K = nb
+        const bool zc = !h->sig_dense_build && op.nb > 0 && p.cl[op.cluster].y0 > 0 &&
+                        p.cl[op.cluster].y1 < p.ny;
+        const int kk = zc ? op.nb : n;
         findgb::GemmOp q = gemm0();
-        q.m = op.c; q.n = n; q.k = n;
+        q.m = op.c; q.n = kk; q.k = kk;
         q.A = M + (int64_t)op.nb * n; q.lda = n; q.sa = escr;
         q.B = Sg; q.ldb = n; q.sb = escr;
         q.D = P; q.ldd = n; q.sd = escr;
@@ -686,7 +727,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
         gemm_ok(q); route(q, 0, la);
         // Q = P G_K^H = G<_K(C, :)
         q = gemm0();
-        q.m = op.c; q.n = n; q.k = n;
+        q.m = op.c; q.n = n; q.k = kk;
         q.A = P; q.lda = n; q.sa = escr;
         q.B = M; q.ldb = n; q.sb = escr; q.opb = 1;
         q.D = Q; q.ldd = n; q.sd = escr;
@@ -779,15 +820,18 @@ Layout make_layout(const find_handle* h, int batch, bool lesser, int64_t scratch
 }
 
 // The FP64 path eliminates by LDL^T (Sec. 4.2) unless FIND_FLAG_LU asks for
-// the LU; a call can use it only when A = A^T, i.e. with the closed-form lead
+// the LU; the mixed paths by LU unless FIND_FLAG_LDL asks for LDL^T.  A call
+// can use LDL^T only when A = A^T, i.e. with the closed-form lead
 // self-energies (Phi diag(sigma) Phi^T); a caller's Sigma takes the LU.
 bool default_ldl(const find_handle* h) {
-  return h->desc.precision == FIND_FP64 && !(h->desc.flags & FIND_FLAG_LU);
+  if (h->desc.flags & FIND_FLAG_LU) return false;
+  return h->desc.precision == FIND_FP64 || (h->desc.flags & FIND_FLAG_LDL);
 }
 
 double workspace_bytes(find_handle* h, int batch, bool lesser, std::string* check_err = nullptr,
                        int ldl = -1) {
   h->ldl_build = ldl < 0 ? default_ldl(h) : ldl != 0;
+  h->sig_dense_build = false;
   Arena ar;
   std::vector<Level> lv;
   int64_t se = 0;
@@ -819,6 +863,9 @@ void drop_graphs(find_handle* h) {
 
 void release(find_handle* h) {
   drop_graphs(h);
+  if (h->rgf_ws) cudaFree(h->rgf_ws);
+  h->rgf_ws = nullptr;
+  h->rgf_batch = 0;
   if (h->ws) cudaFree(h->ws);
   h->ws = nullptr;
   h->batch = 0;
@@ -826,10 +873,15 @@ void release(find_handle* h) {
   h->levels.clear();
 }
 
-int ensure_workspace(find_handle* h, int batch, bool lesser, bool ldl) {
-  if (h->ws && h->batch >= batch && (h->lesser == 1 || !lesser) && h->ldl == ldl) return FIND_OK;
+// dense_sig: the call passes a node-diagonal Sigma<, so no cluster may skip
+// its Sigma update; tables built that way serve every later call too.
+int ensure_workspace(find_handle* h, int batch, bool lesser, bool ldl, bool dense_sig = false) {
+  if (h->ws && h->batch >= batch && (h->lesser == 1 || !lesser) && h->ldl == ldl &&
+      (!dense_sig || h->sig_dense))
+    return FIND_OK;
   release(h);
   h->ldl_build = ldl;
+  h->sig_dense_build = dense_sig;
   Arena ar;
   std::vector<Level> lv;
   int64_t se = 0;
@@ -844,6 +896,7 @@ int ensure_workspace(find_handle* h, int batch, bool lesser, bool ldl) {
   h->batch = batch;
   h->lesser = lesser ? 1 : 0;
   h->ldl = ldl;
+  h->sig_dense = dense_sig;
   Arena real;
   Bounds bc;
   bc.lo = ws;
@@ -898,11 +951,11 @@ const T* at(const find_handle* h, size_t off) {
   return reinterpret_cast<const T*>(h->ws + h->lay.meta + off);
 }
 
-const int kClasses = 18;
+const int kClasses = 19;
 const char* kClassNames[kClasses] = {"lead",     "assemble", "invert",  "lu",   "trsm",
                                      "zgemm32",  "zgemm64",  "extract", "cgemm32", "cgemm64",
                                      "ffgemm32", "ffgemm64", "fftrsm",  "fflu", "ffinvert",
-                                     "tcsplit",  "tcgemm", "ldl"};
+                                     "tcsplit",  "tcgemm", "ldl",     "ffldl"};
 // profiler class of each GEMM launch class 2 * arith + big
 const int kGemmClass[6] = {5, 6, 8, 9, 10, 11};
 
@@ -966,11 +1019,11 @@ void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, boo
   } else {
     for (int c = 0; c < 2; ++c)
       if (lv.ninv[c] > 0) {
-        const bool ldl = h->ldl && c == 0;  // LDL^T: half the flops of the LU
-        timed(h, st, ldl ? 17 : (c ? 13 : 3), lv.fl_inv[c] * (ldl ? 0.5 : 1.0) * nb, 0.0, [&] {
+        const bool ldl = h->ldl;  // LDL^T: half the flops of the LU
+        timed(h, st, ldl ? (c ? 18 : 17) : (c ? 13 : 3), lv.fl_inv[c] * (ldl ? 0.5 : 1.0) * nb, 0.0, [&] {
           if (ldl)
             findgb::launch_ldl(at<findgb::InvOp>(h, lv.inv[c]), lv.ninv[c], lv.inv_max[c], status, e_base,
-                               nb, st, e_off);
+                               nb, st, e_off, c);
           else
             findgb::launch_lu(at<findgb::InvOp>(h, lv.inv[c]), lv.ninv[c], lv.inv_max[c], status, e_base,
                               nb, st, e_off, c);
@@ -980,7 +1033,7 @@ void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, boo
       if (lv.ntrsm[c] > 0)
         timed(h, st, c ? 12 : 4, lv.fl_trsm[c] * nb, 0.0, [&] {
           findgb::launch_trsm(at<findgb::TrsmOp>(h, lv.trsm), at<int>(h, lv.trsm_map[c]), lv.ntrsm[c],
-                              lv.rb, lv.max_s, nb, st, c, e_off, ff_factors(h, c), h->ldl && c == 0);
+                              lv.rb, lv.max_s, nb, st, c, e_off, h->ldl ? 0 : ff_factors(h, c), h->ldl);
         });
   }
   for (int k = 0; k < lv.nstages; ++k) {
@@ -988,7 +1041,7 @@ void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, boo
     const findgb::GemmOp* ops = at<findgb::GemmOp>(h, s.ops);
     for (int c = 0; c < 6; ++c)
       if (s.nmap[c])
-        timed(h, st, kGemmClass[c], s.fl[c] * nb, 0.0, [&] {
+        timed(h, st, kGemmClass[c], ((sym_mask & 1) ? s.fl_sym[c] : s.fl[c]) * nb, 0.0, [&] {
           findgb::launch_gemm(ops, at<int>(h, s.map[c]), s.nmap[c], c & 1, nb, st, c >> 1, e_off,
                               sym_mask);
         });
@@ -1046,7 +1099,7 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
   const int64_t n = (int64_t)p.nx * p.ny, nx = p.nx;
   const bool ldl = default_ldl(h) && !sigL && !sigR;
   int batch = choose_batch(h, nE, lesser, ldl);
-  int rc = ensure_workspace(h, batch, lesser, ldl);
+  int rc = ensure_workspace(h, batch, lesser, ldl, lesser && dles != nullptr);
   if (rc != FIND_OK) return rc;
   batch = std::min(batch, h->batch);
   const Layout& L = h->lay;
@@ -1240,6 +1293,257 @@ int solve(find_handle* h, const double* E, int nE, const double* sigL, const dou
   return FIND_OK;
 }
 
+// ---------------------------------------------------------------- RGF baseline
+// The recursive Green's function method over the Ny transport slices, FP64,
+// all energies of a pass in lockstep:
+//   right-connected sweep  gR_y = (A_yy - C gR_{y+1} C)^-1, y = Ny-1 .. 0
+//   first column           G_00 = gR_0, G_y0 = -gR_y C G_{y-1,0}
+//   left-connected sweep   gL_y = (A_yy - C gL_{y-1} C)^-1, y = 0 .. Ny-1
+//   backward               G_yy = gL_y + gL_y C G_{y+1,y+1} C gL_y,
+//                          G_{y,N-1} = -gL_y C G_{y+1,N-1}
+//   diag G<_yy = diag(G_y0 S<_L G_y0^H) + diag(G_{y,N-1} S<_R G_{y,N-1}^H)
+// (Sigma< on the contact slices only).  Storage per energy: gR and gL of
+// every slice, and nine Nx x Nx working blocks.
+namespace {
+
+// Layout of the RGF workspace for `batch` energies (byte offsets).
+struct RgfLayout {
+  size_t est = 0;                       // complex entries per energy in the block area
+  size_t blk, V, phi, eps, tau, E, sig, modes, SL, SR, G, Gl, stat, meta, total;
+};
+
+RgfLayout rgf_layout(const find_handle* h, int batch, size_t meta_bytes) {
+  const int nx = h->plan.nx, ny = h->plan.ny;
+  const size_t b2 = (size_t)nx * nx, c16 = sizeof(cplx);
+  RgfLayout L;
+  L.est = ((2 * (size_t)ny + 9) * b2 + 15) & ~size_t(15);  // gR[ny], gL[ny], G0 x2, GN x2, D x2, W, T, X
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
+  L.blk = take(L.est * batch * c16);
+  L.V = take((size_t)nx * ny * 8);
+  L.phi = take(b2 * 8);
+  L.eps = take((size_t)nx * 8);
+  L.tau = take((size_t)nx * 8);
+  L.E = take(batch * c16);
+  L.sig = take(batch * b2 * c16);
+  L.modes = take(batch * (size_t)nx * c16);
+  L.SL = take(batch * b2 * c16);
+  L.SR = take(batch * b2 * c16);
+  L.G = take(batch * (size_t)nx * ny * c16);
+  L.Gl = take(batch * (size_t)nx * ny * c16);
+  L.stat = take(256);
+  L.meta = take(meta_bytes);
+  L.total = o;
+  return L;
+}
+
+// The GEMM and inversion descriptors of one RGF pass against `base` (in the
+// order rgf_run consumes them), written into `ar`.
+void rgf_build(const find_handle* h, unsigned char* base, const RgfLayout& L, Arena& ar,
+               size_t* og, size_t* oi, size_t* oz) {
+  const int nx = h->plan.nx, ny = h->plan.ny;
+  const size_t b2 = (size_t)nx * nx;
+  const int64_t es = (int64_t)L.est;
+  cplx* B0 = reinterpret_cast<cplx*>(base + L.blk);
+  auto blk = [&](size_t k) { return B0 + k * b2; };
+  const size_t wk = 2 * (size_t)ny;
+  cplx* G0[2] = {blk(wk), blk(wk + 1)};
+  cplx* GN[2] = {blk(wk + 2), blk(wk + 3)};
+  cplx* D[2] = {blk(wk + 4), blk(wk + 5)};
+  cplx* Wb = blk(wk + 6);
+  cplx* Tb = blk(wk + 7);
+  cplx* Xb = blk(wk + 8);
+  cplx* SL = reinterpret_cast<cplx*>(base + L.SL);
+  cplx* SR = reinterpret_cast<cplx*>(base + L.SR);
+  std::vector<findgb::GemmOp> g;
+  std::vector<findgb::InvOp> inv;
+  auto mm = [&](const cplx* A, const cplx* B, int64_t sb, const cplx* C, cplx* Dd, double alpha) {
+    findgb::GemmOp q = gemm0();
+    q.m = nx; q.n = nx; q.k = nx;
+    q.A = A; q.lda = nx; q.sa = es; q.alpha = alpha;
+    q.B = B; q.ldb = nx; q.sb = sb;
+    if (C) { q.C = C; q.ldc = nx; q.sc = es; q.beta = 1.0; }
+    q.D = Dd; q.ldd = nx; q.sd = es;
+    q.tiles_n = (nx + 63) / 64;
+    g.push_back(q);
+  };
+  for (int y = 0; y < ny; ++y) {
+    inv.push_back(findgb::InvOp{blk(y), es, nx, nx, nullptr, 0, nullptr});            // gR_y
+    inv.push_back(findgb::InvOp{blk((size_t)ny + y), es, nx, nx, nullptr, 0, nullptr}); // gL_y
+  }
+  // column pass, op 2y: G_y0 = -gR_y W;  op 2y+1: X = G_y0 S<_L
+  for (int y = 0; y < ny; ++y) {
+    mm(blk(y), Wb, es, nullptr, G0[y & 1], -1.0);
+    mm(y == 0 ? blk(0) : G0[y & 1], SL, (int64_t)b2, nullptr, Xb, 1.0);
+  }
+  // backward, op 2ny + 4y .. +3: T = gL_y Q; D_y = gL_y + T gL_y; GN_y = -gL_y W;
+  // X = GN_y S<_R (GN_{ny-1} = gL_{ny-1})
+  for (int y = 0; y < ny; ++y) {
+    cplx* gl = blk((size_t)ny + y);
+    mm(gl, Wb, es, nullptr, Tb, 1.0);
+    mm(Tb, gl, es, gl, D[y & 1], 1.0);
+    mm(gl, Wb, es, nullptr, GN[y & 1], -1.0);
+    mm(y == ny - 1 ? gl : GN[y & 1], SR, (int64_t)b2, nullptr, Xb, 1.0);
+  }
+  *og = ar.put(g);
+  *oi = ar.put(inv);
+  std::vector<int> zmap((size_t)((nx + 63) / 64) * ((nx + 63) / 64), 0);
+  *oz = ar.put(zmap);
+}
+
+int rgf_solve(find_handle* h, const double* E, int nE, double fL, double fR, double* G, double* Gl,
+              void* stream) {
+  if (!h) return fail(nullptr, FIND_EINVAL, "null handle");
+  if (nE < 0) return fail(h, FIND_EINVAL, "nE < 0");
+  if (nE == 0) return FIND_OK;
+  if (!E || !G || !Gl) return fail(h, FIND_EINVAL, "E, diagG and diagGl must not be NULL");
+  DeviceGuard guard(h->desc.device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const findgb::Plan& p = h->plan;
+  const int nx = p.nx, ny = p.ny;
+  const int64_t n = (int64_t)nx * ny;
+  const size_t b2 = (size_t)nx * nx;
+  int batch = h->desc.max_batch > 0 ? std::min(h->desc.max_batch, nE) : 0;
+  if (batch == 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    if (h->rgf_ws) fr += rgf_layout(h, h->rgf_batch, h->rgf_meta_bytes).total;
+    const double per = (double)(rgf_layout(h, 2, 0).total - rgf_layout(h, 1, 0).total);
+    batch = std::max(1, std::min({(int)(0.6 * (double)fr / per), 64, nE}));
+  }
+  if (!h->rgf_ws || h->rgf_batch < batch) {
+    if (h->rgf_ws) cudaFree(h->rgf_ws);
+    h->rgf_ws = nullptr;
+    Arena sizing;
+    size_t t3[3];
+    rgf_build(h, nullptr, rgf_layout(h, batch, 0), sizing, &t3[0], &t3[1], &t3[2]);
+    const RgfLayout L = rgf_layout(h, batch, sizing.buf.size());
+    unsigned char* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, L.total);
+    if (e != cudaSuccess) return cuda_fail(h, e, "RGF workspace allocation");
+    Arena real;
+    rgf_build(h, base, L, real, &h->rgf_tab[0], &h->rgf_tab[1], &h->rgf_tab[2]);
+    e = cudaMemcpy(base + L.V, h->V.data(), h->V.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + L.phi, h->phi.data(), h->phi.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + L.eps, h->eps.data(), h->eps.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + L.tau, h->tau.data(), h->tau.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + L.meta, real.buf.data(), real.buf.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(base);
+      return cuda_fail(h, e, "RGF workspace upload");
+    }
+    h->rgf_ws = base;
+    h->rgf_batch = batch;
+    h->rgf_meta_bytes = sizing.buf.size();
+  }
+  batch = std::min(batch, h->rgf_batch);
+  const RgfLayout L = rgf_layout(h, h->rgf_batch, h->rgf_meta_bytes);
+  unsigned char* base = h->rgf_ws;
+  const int64_t es = (int64_t)L.est;
+  cplx* B0 = reinterpret_cast<cplx*>(base + L.blk);
+  auto blk = [&](size_t k) { return B0 + k * b2; };
+  const size_t wk = 2 * (size_t)ny;
+  cplx* G0[2] = {blk(wk), blk(wk + 1)};
+  cplx* GN[2] = {blk(wk + 2), blk(wk + 3)};
+  cplx* D[2] = {blk(wk + 4), blk(wk + 5)};
+  cplx* Wb = blk(wk + 6);
+  cplx* Xb = blk(wk + 8);
+  auto gops = reinterpret_cast<const findgb::GemmOp*>(base + L.meta + h->rgf_tab[0]);
+  auto iops = reinterpret_cast<const findgb::InvOp*>(base + L.meta + h->rgf_tab[1]);
+  auto zmap = reinterpret_cast<const int*>(base + L.meta + h->rgf_tab[2]);
+  const int ntiles = ((nx + 63) / 64) * ((nx + 63) / 64);
+  int* status = reinterpret_cast<int*>(base + L.stat);
+  cplx* dE = reinterpret_cast<cplx*>(base + L.E);
+  cplx* sig = reinterpret_cast<cplx*>(base + L.sig);
+  cplx* SL = reinterpret_cast<cplx*>(base + L.SL);
+  cplx* SR = reinterpret_cast<cplx*>(base + L.SR);
+  const bool dG = device_accessible(G), dGl = device_accessible(Gl);
+  cudaError_t e = cudaMemsetAsync(status, 0x7f, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
+  auto gemm = [&](int op, int nb) { findgb::launch_gemm(gops + op, zmap, ntiles, 1, nb, st, 0, 0, 0); };
+  for (int e0 = 0; e0 < nE; e0 += batch) {
+    const int nb = std::min(batch, nE - e0);
+    e = cudaMemcpyAsync(dE, E + 2 * (int64_t)e0, nb * sizeof(cplx), cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "energy copy");
+    findgb::launch_lead_modes(dE, nb, reinterpret_cast<const double*>(base + L.eps),
+                              reinterpret_cast<const double*>(base + L.tau), nx,
+                              reinterpret_cast<cplx*>(base + L.modes), st);
+    findgb::launch_lead_dense(reinterpret_cast<cplx*>(base + L.modes), reinterpret_cast<const double*>(base + L.phi),
+                              nx, nb, sig, st);
+    findgb::launch_rgf_lesser(sig, nx, fL, SL, nb, st);
+    findgb::launch_rgf_lesser(sig, nx, fR, SR, nb, st);
+    findgb::RgfSlice s;
+    s.nx = nx; s.ny = ny; s.stencil = p.stencil;
+    s.t = h->desc.t; s.tp = h->desc.tp; s.onsite0 = h->desc.onsite0;
+    s.V = reinterpret_cast<const double*>(base + L.V);
+    s.E = dE; s.sigL = sig; s.sigR = sig;
+    cplx* oG = dG ? reinterpret_cast<cplx*>(G) + (int64_t)e0 * n : reinterpret_cast<cplx*>(base + L.G);
+    cplx* oGl = dGl ? reinterpret_cast<cplx*>(Gl) + (int64_t)e0 * n : reinterpret_cast<cplx*>(base + L.Gl);
+    // right-connected sweep
+    for (int y = ny - 1; y >= 0; --y) {
+      findgb::launch_rgf_block(s, y, y < ny - 1 ? blk(y + 1) : nullptr, es, blk(y), es, nb, st);
+      findgb::launch_invert(iops + 2 * y, 1, nx, status, e0, nb, st);
+    }
+    // first column G_y0 and its share of diag G<
+    for (int y = 0; y < ny; ++y) {
+      if (y > 0) {
+        findgb::launch_rgf_cprod(s, y == 1 ? blk(0) : G0[(y - 1) & 1], es, Wb, es, 1.0, 0, nb, st);
+        gemm(2 * y, nb);
+      }
+      gemm(2 * y + 1, nb);
+      findgb::launch_rgf_diag(s, Xb, y == 0 ? blk(0) : G0[y & 1], es, oGl + (int64_t)y * nx, n, 0, nullptr,
+                              nullptr, nb, st);
+    }
+    // left-connected sweep
+    for (int y = 0; y < ny; ++y) {
+      findgb::launch_rgf_block(s, y, y > 0 ? blk((size_t)ny + y - 1) : nullptr, es, blk((size_t)ny + y), es, nb, st);
+      findgb::launch_invert(iops + 2 * y + 1, 1, nx, status, e0, nb, st);
+    }
+    // backward: G_yy, G_{y,N-1}, diag G, the second share of diag G<
+    const int ob = 2 * ny;
+    const cplx* prevD = blk((size_t)ny + ny - 1);
+    const cplx* prevGN = prevD;
+    gemm(ob + 4 * (ny - 1) + 3, nb);
+    findgb::launch_rgf_diag(s, Xb, prevGN, es, oGl + (int64_t)(ny - 1) * nx, n, 1, prevD,
+                            oG + (int64_t)(ny - 1) * nx, nb, st);
+    for (int y = ny - 2; y >= 0; --y) {
+      findgb::launch_rgf_cprod(s, prevD, es, Wb, es, 1.0, 1, nb, st);  // W = C G_{y+1,y+1} C
+      gemm(ob + 4 * y, nb);                                           // T = gL_y W
+      gemm(ob + 4 * y + 1, nb);                                       // D_y = gL_y + T gL_y
+      findgb::launch_rgf_cprod(s, prevGN, es, Wb, es, 1.0, 0, nb, st); // W = C G_{y+1,N-1}
+      gemm(ob + 4 * y + 2, nb);                                       // GN_y = -gL_y W
+      gemm(ob + 4 * y + 3, nb);                                       // X = GN_y S<_R
+      findgb::launch_rgf_diag(s, Xb, GN[y & 1], es, oGl + (int64_t)y * nx, n, 1, D[y & 1],
+                              oG + (int64_t)y * nx, nb, st);
+      prevD = D[y & 1];
+      prevGN = GN[y & 1];
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "RGF launch");
+    if (!dG) {
+      e = cudaMemcpyAsync(G + 2 * (int64_t)e0 * n, oG, nb * n * sizeof(cplx), cudaMemcpyDefault, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "diagG copy-out");
+    }
+    if (!dGl) {
+      e = cudaMemcpyAsync(Gl + 2 * (int64_t)e0 * n, oGl, nb * n * sizeof(cplx), cudaMemcpyDefault, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "diagGl copy-out");
+    }
+  }
+  int hs = 0x7f7f7f7f;
+  e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "RGF solve");
+  if (hs != 0x7f7f7f7f) {
+    char buf[128];
+    std::snprintf(buf, sizeof buf, "exactly zero pivot at energy index %d", hs);
+    return fail(h, FIND_ESINGULAR, buf);
+  }
+  h->err.clear();
+  return FIND_OK;
+}
+
+}  // namespace
+
 // ---------------------------------------------------------------- fixed device scratch
 // Device memory of find_solve_diag_static, for callers that cannot allocate
 // device memory.  It lives as long as the library stays loaded, on every
@@ -1283,9 +1587,9 @@ void run_level_static(find_handle* h, const StaticView& sv, const Level& lv,
                             lv.inv_max[c], status, e_base, nb, st, 0, c & 1, c >> 1);
   } else {
     for (int c = 0; c < 2; ++c) {
-      if (sv.ldl == 1 && c == 0)
+      if (sv.ldl == 1)
         findgb::launch_ldl(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv[c])), lv.ninv[c],
-                           lv.inv_max[c], status, e_base, nb, st, 0);
+                           lv.inv_max[c], status, e_base, nb, st, 0, c);
       else
         findgb::launch_lu(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv[c])), lv.ninv[c],
                           lv.inv_max[c], status, e_base, nb, st, 0, c);
@@ -1293,7 +1597,7 @@ void run_level_static(find_handle* h, const StaticView& sv, const Level& lv,
     for (int c = 0; c < 2; ++c)
       findgb::launch_trsm(reinterpret_cast<const findgb::TrsmOp*>(meta(lv.trsm)),
                           reinterpret_cast<const int*>(meta(lv.trsm_map[c])), lv.ntrsm[c], lv.rb,
-                          lv.max_s, nb, st, c, 0, ff_factors(h, c), sv.ldl == 1 && c == 0);
+                          lv.max_s, nb, st, c, 0, sv.ldl == 1 ? 0 : ff_factors(h, c), sv.ldl == 1);
   }
   for (int k = 0; k < lv.nstages; ++k) {
     const Stage& s = lv.st[k];
@@ -1329,12 +1633,16 @@ int solve_static(find_handle* h, const double* E, int nE, const double* sigL, co
   StaticView& sv = h->sview;
   const int ldl = (default_ldl(h) && !sigL && !sigR) ? 1 : 0;
   if (sv.base != base || sv.ldl != ldl) {
-    // size the largest energy batch that fits, then lay the tables out on it
+    // the largest energy batch that fits: the footprint is an affine
+    // function of the batch (per-energy slabs plus fixed tables), taken from
+    // two table builds and confirmed by a third
     int batch = 0;
-    double need1 = workspace_bytes(h, 1, false, nullptr, ldl);
-    for (int b = 1; b <= 64; ++b) {
-      if (workspace_bytes(h, b, false, nullptr, ldl) > (double)kStaticScratchBytes) break;
-      batch = b;
+    const double need1 = workspace_bytes(h, 1, false, nullptr, ldl);
+    if (need1 <= (double)kStaticScratchBytes) {
+      const double per = std::max(1.0, workspace_bytes(h, 2, false, nullptr, ldl) - need1);
+      batch = std::max(1, std::min(64, 1 + (int)(((double)kStaticScratchBytes - need1) / per)));
+      while (batch > 1 && workspace_bytes(h, batch, false, nullptr, ldl) > (double)kStaticScratchBytes)
+        --batch;
     }
     if (batch == 0) {
       char buf[192];
@@ -1471,7 +1779,8 @@ int find_create(const find_desc* d, find_handle** out) {
   if (d->tc_slices < 0 || d->tc_slices > 12 || d->tc_slices_mixed < 0 || d->tc_slices_mixed > 12 ||
       d->tc_min < 0)
     return fail(nullptr, FIND_EINVAL, "tc_slices and tc_slices_mixed must be in [0, 12], tc_min >= 0");
-  if (d->flags & ~(FIND_FLAG_FULL_U | FIND_FLAG_SYM_U | FIND_FLAG_GRAPH | FIND_FLAG_NO_TC | FIND_FLAG_LU))
+  if (d->flags & ~(FIND_FLAG_FULL_U | FIND_FLAG_SYM_U | FIND_FLAG_GRAPH | FIND_FLAG_NO_TC | FIND_FLAG_LU |
+                   FIND_FLAG_LDL))
     return fail(nullptr, FIND_EINVAL, "unknown bit in flags");
   if (d->energy_group < 0 || d->sigma_c64_depth < 0)
     return fail(nullptr, FIND_EINVAL, "energy_group and sigma_c64_depth must be >= 0");
@@ -1551,6 +1860,11 @@ int find_workspace_bytes(const find_handle* h, int batch, int lesser, double* by
 int find_solve_diag(find_handle* h, const double* E, int nE, const double* sigmaL,
                     const double* sigmaR, double* diagG, void* stream) {
   return solve(h, E, nE, sigmaL, sigmaR, 0.0, 0.0, nullptr, 0, diagG, nullptr, nullptr, stream, false);
+}
+
+int find_rgf_solve_lesser(find_handle* h, const double* E, int nE, double fL, double fR,
+                          double* diagG, double* diagGl, void* stream) {
+  return rgf_solve(h, E, nE, fL, fR, diagG, diagGl, stream);
 }
 
 int find_solve_diag_static(find_handle* h, const double* E, int nE, const double* sigmaL,

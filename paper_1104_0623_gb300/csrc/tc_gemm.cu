@@ -229,14 +229,18 @@ __device__ __forceinline__ I fixed_digits(double v, int e, int P) {
   return (b >> 63) ? -x : x;
 }
 
-// The next signed base-64 digit (MSB first) of X and the remainder after it:
-// d = floor((rem + h) / w), w = 2^shift, h = w / 2; rem -= d w.
+// The signed base-64 digits of X, least significant first, with constant
+// shifts only: every digit below the top one is the balanced residue of the
+// remainder mod 64, in [-32, 31], and the top digit takes what remains
+// (|X| <= 2^P = 32 * 64^(nsl-1) keeps it within [-32, 32]).  Every digit is
+// an integer of at most 6 bits, as the exactness of the planes' products
+// requires.
 template <class I>
-__device__ __forceinline__ int next_digit(I& rem, int shift) {
-  const I h = shift > 0 ? ((I)1 << (shift - 1)) : (I)0;
-  const I d = (rem + h) >> shift;
-  rem -= d << shift;
-  return (int)d;
+__device__ __forceinline__ int low_digit(I& rem, bool top) {
+  if (top) return (int)rem;
+  const int d = (int)(((unsigned)rem + 32u) & 63u) - 32;
+  rem = (rem - (I)d) >> 6;
+  return d;
 }
 
 // bf16 bits of d * 2^-6s for a small integer d (|d| <= 32), exact.
@@ -334,18 +338,33 @@ __global__ void __launch_bounds__(256) k_tc_scale(const TcOp* __restrict__ ops,
   if (lane == 0 && best != kNoExp) atomicMax(sc + (kind == 0 ? op.ascale : op.bscale) + r, best);
 }
 
-// The nsl digit planes (re, im interleaved by plane) of one entry.
+// The digit planes of two adjacent entries (each written only if its flag is
+// set; both: one 4-byte store per plane).
 template <class I>
-__device__ __forceinline__ void write_digits(cplx v, int ex, int P, int nsl, unsigned short* dst,
-                                             int64_t plane_stride) {
-  I xr = (ex == kNoExp) ? (I)0 : fixed_digits<I>(v.x, ex, P);
-  I xi = (ex == kNoExp) ? (I)0 : fixed_digits<I>(v.y, ex, P);
-  for (int s = 0; s < nsl; ++s) {
-    const int shift = 6 * (nsl - 1 - s);
+__device__ __forceinline__ void write_digit_pair(cplx v0, cplx v1, bool m0, bool m1, int ex, int P,
+                                                 int nsl, unsigned short* dst, int64_t plane_stride) {
+  I r0 = (ex == kNoExp) ? (I)0 : fixed_digits<I>(v0.x, ex, P);
+  I i0 = (ex == kNoExp) ? (I)0 : fixed_digits<I>(v0.y, ex, P);
+  I r1 = (ex == kNoExp) ? (I)0 : fixed_digits<I>(v1.x, ex, P);
+  I i1 = (ex == kNoExp) ? (I)0 : fixed_digits<I>(v1.y, ex, P);
+  for (int s = nsl - 1; s >= 0; --s) {  // planes from the least significant
     const float scl = pow2f(-6 * s);
-    const int dr = next_digit(xr, shift), di = next_digit(xi, shift);
-    dst[(int64_t)(2 * s) * plane_stride] = digit_bf16(dr, scl);
-    dst[(int64_t)(2 * s + 1) * plane_stride] = digit_bf16(di, scl);
+    const unsigned short a0 = digit_bf16(low_digit(r0, s == 0), scl);
+    const unsigned short b0 = digit_bf16(low_digit(i0, s == 0), scl);
+    const unsigned short a1 = digit_bf16(low_digit(r1, s == 0), scl);
+    const unsigned short b1 = digit_bf16(low_digit(i1, s == 0), scl);
+    unsigned short* pr = dst + (int64_t)(2 * s) * plane_stride;
+    unsigned short* pi = dst + (int64_t)(2 * s + 1) * plane_stride;
+    if (m0 && m1) {
+      *reinterpret_cast<uint32_t*>(pr) = (uint32_t)a0 | ((uint32_t)a1 << 16);
+      *reinterpret_cast<uint32_t*>(pi) = (uint32_t)b0 | ((uint32_t)b1 << 16);
+    } else if (m0) {
+      pr[0] = a0;
+      pi[0] = b0;
+    } else {
+      pr[1] = a1;
+      pi[1] = b1;
+    }
   }
 }
 
@@ -374,35 +393,39 @@ __global__ void __launch_bounds__(256) k_tc_split_rows(const TcOp* __restrict__ 
       ((int64_t)(side ? op.brow : op.arow) + r) * slab.pitch;
   const int64_t plane_stride = (int64_t)rows_pad * slab.pitch;  // between consecutive planes
   const int ex = (r < valid) ? sc[(side ? op.bscale : op.ascale) + r] : kNoExp;
-  for (int k = lane; k < op.kp; k += 32) {
+  // entry k of the row, and whether this kernel writes it (segments of plain B
+  // operands are k_tc_split_cols')
+  auto fetch = [&](int k, cplx& v) -> bool {
+    v = make_double2(0.0, 0.0);
     const bool in1 = k < op.k1, in2 = k >= op.k1p && k < op.k1p + op.k2;
-    cplx v = make_double2(0.0, 0.0);
-    bool mine = true;  // this kernel writes the position
-    if (r < valid && ex != kNoExp && (in1 || in2)) {
-      const int part = in1 ? 0 : 1;
-      const int kk = in1 ? k : k - op.k1p;
-      if (side == 0) {
-        const cplx* A = part ? op.A2 + (int64_t)e * op.sa2 : op.A1 + (int64_t)e * op.sa1;
-        const int ld = part ? op.lda2 : op.lda1;
-        v = A[(int64_t)r * ld + kk];
-        if (part ? op.neg2 : op.neg1) v = make_double2(-v.x, -v.y);
-      } else {
-        const int opb = part ? op.opb2 : op.opb1;
-        if (opb == 0) {
-          mine = false;
-        } else {
-          const cplx* B = part ? op.B2 + (int64_t)e * op.sb2 : op.B1 + (int64_t)e * op.sb1;
-          const int ld = part ? op.ldb2 : op.ldb1;
-          v = B[(int64_t)r * ld + kk];
-          if (opb == 1) v.y = -v.y;  // op(B) = B^H; opb 2: B^T
-        }
-      }
+    if (r >= valid || ex == kNoExp || !(in1 || in2)) return true;
+    const int part = in1 ? 0 : 1;
+    const int kk = in1 ? k : k - op.k1p;
+    if (side == 0) {
+      const cplx* A = part ? op.A2 + (int64_t)e * op.sa2 : op.A1 + (int64_t)e * op.sa1;
+      const int ld = part ? op.lda2 : op.lda1;
+      v = A[(int64_t)r * ld + kk];
+      if (part ? op.neg2 : op.neg1) v = make_double2(-v.x, -v.y);
+      return true;
     }
-    if (!mine) continue;
+    const int opb = part ? op.opb2 : op.opb1;
+    if (opb == 0) return false;
+    const cplx* B = part ? op.B2 + (int64_t)e * op.sb2 : op.B1 + (int64_t)e * op.sb1;
+    const int ld = part ? op.ldb2 : op.ldb1;
+    v = B[(int64_t)r * ld + kk];
+    if (opb == 1) v.y = -v.y;  // op(B) = B^H; opb 2: B^T
+    return true;
+  };
+  // two adjacent positions per lane (kp and every segment start are multiples
+  // of 64, so a pair never straddles a segment and its 4 bytes are aligned)
+  for (int k = 2 * lane; k < op.kp; k += 64) {
+    cplx v0, v1;
+    const bool m0 = fetch(k, v0), m1 = fetch(k + 1, v1);
+    if (!m0 && !m1) continue;
     if (nsl <= 10)
-      write_digits<long long>(v, ex, P, nsl, base + k, plane_stride);
+      write_digit_pair<long long>(v0, v1, m0, m1, ex, P, nsl, base + k, plane_stride);
     else
-      write_digits<__int128>(v, ex, P, nsl, base + k, plane_stride);
+      write_digit_pair<__int128>(v0, v1, m0, m1, ex, P, nsl, base + k, plane_stride);
   }
 }
 
@@ -434,14 +457,13 @@ __device__ __forceinline__ void split_cols_body(const TcOp* __restrict__ ops, co
   const int64_t plane_stride = (int64_t)rows_pad * slab.pitch;
   unsigned short* base = slab.b + (int64_t)e * slab.plane_estride + (int64_t)op.brow * slab.pitch;
   const int kw = min(kTcK, K - k0);  // positions of this block inside the part
-  for (int s = 0; s < nsl; ++s) {
-    const int shift = 6 * (nsl - 1 - s);
+  for (int s = nsl - 1; s >= 0; --s) {  // planes from the least significant
     const float scl = pow2f(-6 * s);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int kk = warp + 8 * q;
-      tile[0][lane][kk] = digit_bf16(next_digit(xr[q], shift), scl);
-      tile[1][lane][kk] = digit_bf16(next_digit(xi[q], shift), scl);
+      tile[0][lane][kk] = digit_bf16(low_digit(xr[q], s == 0), scl);
+      tile[1][lane][kk] = digit_bf16(low_digit(xi[q], s == 0), scl);
     }
     __syncthreads();
     // 2 planes x 32 rows, a warp per row, two positions per lane (K-contiguous);
@@ -564,7 +586,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (*(volatile int*)&abort_sh) { ok = false; break; }
             unsigned char* st = smem + stage * kTcStageBytes;
             mbar_expect_tx(&full_bar[stage], kTcStageBytes);
-            const int k = ks * kTcK;
+            // odd groups run over K backwards: a group starts on the tiles the
+            // previous one loaded last, while they are still in L2 (the
+            // order of an exact diagonal's sum does not change its value)
+            const int k = ((g & 1) ? ksteps - 1 - ks : ks) * kTcK;
             const int ra = op.arow + (2 * s) * Mpad + tm * kTcM;
             const int rb = op.brow + (2 * tt) * Npad + tn * kTcN;
             tma_load_3d(st, &mapA, &full_bar[stage], k, ra, e);

@@ -55,12 +55,13 @@ def test_create_rejects_bad_arguments(F, kw, msg):
 
 def test_create_rejects_unknown_flags(F):
     import ctypes
-    d = F._abi.find_desc(4, 4, 5, 1.0, 0.0, None, 4.0, 8, F.FIND_FP64, 0, 0, 2, 0, 0, 0, 32, 0)
+    d = F._abi.find_desc(4, 4, 5, 1.0, 0.0, None, 4.0, 8, F.FIND_FP64, 0, 0, 2, 0, 0, 0, 64, 0)
     h = ctypes.c_void_p()
     rc = F._abi.load().find_create(ctypes.byref(d), ctypes.byref(h))
     assert rc == 1 and "flags" in F.find_last_error(None)
-    ok = F.Find(4, 4, full_u=True, sym_u=True, graph=True, tensor_cores=False, ldl=False)  # every known bit
-    ok.close()
+    for ldl in (False, True):  # every known bit
+        ok = F.Find(4, 4, full_u=True, sym_u=True, graph=True, tensor_cores=False, ldl=ldl)
+        ok.close()
 
 
 def test_create_rejects_bad_plane_counts(F):

@@ -54,6 +54,31 @@ def test_static_scratch_matches_allocating_solve(F):
     f.close()
 
 
+def test_static_scratch_alternating_handles_host_buffers_and_mixed_path(F):
+    """Two handles on different meshes called A, B, A on one stream (each call
+    re-uploads its own tables into the shared array); host numpy energies and
+    outputs over several passes (copied out pass by pass); a float-float handle
+    against its own allocating solve."""
+    import torch
+    lib = F._abi.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    fa = F.Find.from_mesh(W.Mesh(28, 36, 9, 1.0, 0.2, -1.0, 1.0, 71), leaf=6)
+    fb = F.Find.from_mesh(W.Mesh(20, 24, 5, 1.0, 0.0, -0.5, 0.5, 72), leaf=8)
+    fm = F.Find.from_mesh(W.Mesh(24, 30, 5, 1.0, 0.0, -0.5, 0.5, 73), leaf=8, precision="mixed_ff")
+    Es = W.energy_grid(0.3, 3.9, 23)  # several passes through the fixed array
+    for f, tol in ((fa, TOL), (fb, TOL), (fa, TOL), (fm, 1e-7)):
+        ref = f.solve_diag(np.ascontiguousarray(Es))
+        out = np.full((len(Es), f.n), np.nan, dtype=np.complex128)
+        E = np.ascontiguousarray(Es)
+        rc = lib.find_solve_diag_static(f.handle, E.ctypes.data, len(Es), None, None,
+                                        out.ctypes.data, stream)
+        assert rc == 0, lib.find_last_error(f.handle).decode()
+        for k in range(len(Es)):
+            assert rel(out[k], ref[k]) <= tol, (f.nx, f.ny, k, rel(out[k], ref[k]))
+    for f in (fa, fb, fm):
+        f.close()
+
+
 def test_static_scratch_rejects_a_mesh_that_does_not_fit(F):
     import torch
     lib = F._abi.load()
