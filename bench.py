@@ -51,6 +51,7 @@ FF_INST_PER_CMAC = {"ffgemm32": 48.75, "ffgemm64": 48.75, "fftrsm": 54.0, "fflu"
                     "ffinvert": 54.0, "ffldl": 54.0}
 # digit-plane pairs per complex multiply-add of the tensor-core products on the
 # mixed path (9 planes: pairs with s + t <= 8) and real bf16 products per pair
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 at the maximum SM clock
 TC_PLANES_MIXED = 9
 TC_PAIRS = TC_PLANES_MIXED * (TC_PLANES_MIXED + 1) // 2
 TC_REAL_PER_PAIR = 4
@@ -383,10 +384,15 @@ def kernel_roofline(p, f_sm, n_sm, peaks):
         ffma = peaks.get("ffma_tflops_probe")
         out["frac_of_ffma_8flops"] = alg / ffma if ffma else None
     else:
-        peak = peaks.get("dmma_tflops_probe") or peaks.get("dfma_tflops_probe")
-        out.update(bound="alu", achieved=alg, peak=peak, unit="TFLOP/s",
-                   frac=alg / peak if peak else None,
-                   peak_source="FP64: the DMMA probe of this run (find_peak_probe kind 2)")
+        # FP64: the nominal 1.25 TFLOP/s at the sampled clock, or the DMMA
+        # probe of this run if that is higher (a GEMM with a full FP64 pipe
+        # runs above the probe's independent-chain loop)
+        nominal = FP64_NOMINAL_TFLOPS * f_sm / SM_MAX_MHZ_NOMINAL
+        probe = peaks.get("dmma_tflops_probe") or peaks.get("dfma_tflops_probe") or 0.0
+        peak = max(nominal, probe)
+        out.update(bound="alu", achieved=alg, peak=peak, unit="TFLOP/s", frac=alg / peak,
+                   peak_source=f"FP64: max(nominal 1.25 TFLOP/s x {f_sm:.0f}/2070 MHz, "
+                               f"DMMA probe {probe:.3f})")
     return out
 
 

@@ -1139,7 +1139,7 @@ __device__ __forceinline__ void rank_update(T* Y, const cplx* a, int ld, int s, 
 }
 
 template <bool DF, bool FF, bool LDL>
-__global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
+__global__ void __launch_bounds__(512) k_trsm(const TrsmOp* __restrict__ ops,
                                               const int* __restrict__ tile_op, int rb, int e_off) {
   typedef TrsmArith<DF> X;
   typedef typename X::T T;
@@ -1331,6 +1331,13 @@ void launch_assemble(const AsmOp* ops, const int* row_op, int nrows, const Pos* 
   k_assemble<<<grid, 256, 0, st>>>(ops, row_op, pos, P, lesser, e_off, nE);
 }
 
+// Threads per block of the factorisations and inversions: every entry sees
+// the same operations in the same order whatever the count (warps take rows,
+// the pivot search reduces over all warps), so the results do not depend on it.
+int inv_threads(int max_s) {
+  return max_s <= kSmallBlock ? 128 : (max_s <= 2 * kSmallBlock ? 256 : kInvThreads);
+}
+
 void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
                    cudaStream_t st, int e_off, int df, int in_smem) {
   if (nops == 0 || max_s == 0) return;
@@ -1354,10 +1361,11 @@ void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_bas
       k_invert_smem<false><<<grid, kInvThreads, smem, st>>>(ops, status, e_base, e_off);
   } else {
     size_t smem = (size_t)max_s * (2 * sizeof(cplx) + sizeof(int));
+    const int nt = inv_threads(max_s);
     if (df)
-      k_invert<true><<<grid, kInvThreads, smem, st>>>(ops, status, e_base, e_off);
+      k_invert<true><<<grid, nt, smem, st>>>(ops, status, e_base, e_off);
     else
-      k_invert<false><<<grid, kInvThreads, smem, st>>>(ops, status, e_base, e_off);
+      k_invert<false><<<grid, nt, smem, st>>>(ops, status, e_base, e_off);
   }
 }
 
@@ -1374,9 +1382,9 @@ void launch_lu(const InvOp* ops, int nops, int max_s, int* status, int e_base, i
       attr_set = true;
     }
     const size_t smem = (size_t)kLuPanel * max_s * sizeof(float4);
-    k_lu_panel<kLuPanel><<<grid, kInvThreads, smem, st>>>(ops, status, e_base, e_off);
+    k_lu_panel<kLuPanel><<<grid, inv_threads(max_s), smem, st>>>(ops, status, e_base, e_off);
   } else {
-    k_lu<false><<<grid, kInvThreads, kMaxInvert * sizeof(cplx), st>>>(ops, status, e_base, e_off);
+    k_lu<false><<<grid, inv_threads(max_s), kMaxInvert * sizeof(cplx), st>>>(ops, status, e_base, e_off);
   }
 }
 
@@ -1404,16 +1412,20 @@ void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int 
   }
   size_t smem = (size_t)rb * max_s * sizeof(cplx) + (size_t)max_s * sizeof(int);
   dim3 grid(ntiles, nE);
+  // a block whose rows take more than half an SM's shared memory runs alone
+  // on its SM: give it 16 warps instead of 8 for the rank updates (the
+  // panel solves keep their 4 warps; every entry sees the same operations)
+  const int nt = smem > 113 * 1024 ? 512 : 256;
   if (ldl && df)
-    k_trsm<true, false, true><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
+    k_trsm<true, false, true><<<grid, nt, smem, st>>>(ops, tile_op, rb, e_off);
   else if (ldl)
-    k_trsm<false, false, true><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
+    k_trsm<false, false, true><<<grid, nt, smem, st>>>(ops, tile_op, rb, e_off);
   else if (df && ff_factors)
-    k_trsm<true, true, false><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
+    k_trsm<true, true, false><<<grid, nt, smem, st>>>(ops, tile_op, rb, e_off);
   else if (df)
-    k_trsm<true, false, false><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
+    k_trsm<true, false, false><<<grid, nt, smem, st>>>(ops, tile_op, rb, e_off);
   else
-    k_trsm<false, false, false><<<grid, 256, smem, st>>>(ops, tile_op, rb, e_off);
+    k_trsm<false, false, false><<<grid, nt, smem, st>>>(ops, tile_op, rb, e_off);
 }
 
 void launch_ldl(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
@@ -1428,10 +1440,11 @@ void launch_ldl(const InvOp* ops, int nops, int max_s, int* status, int e_base, 
     attr_set = true;
   }
   dim3 grid(nops, nE);
+  const int nt = inv_threads(max_s);
   if (df)
-    k_ldl<true><<<grid, kInvThreads, 2 * (size_t)max_s * sizeof(float4), st>>>(ops, status, e_base, e_off);
+    k_ldl<true><<<grid, nt, 2 * (size_t)max_s * sizeof(float4), st>>>(ops, status, e_base, e_off);
   else
-    k_ldl<false><<<grid, kInvThreads, 2 * (size_t)max_s * sizeof(cplx), st>>>(ops, status, e_base, e_off);
+    k_ldl<false><<<grid, nt, 2 * (size_t)max_s * sizeof(cplx), st>>>(ops, status, e_base, e_off);
 }
 
 void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,

@@ -109,6 +109,10 @@ void launch_lead_dense(const cplx* sig_modes, const double* phi, int nx, int nE,
 // (grid.y = nE); independent energy groups can run on separate streams.
 void launch_assemble(const AsmOp* ops, const int* row_op, int nrows, const Pos* pos,
                      const DevProblem& P, int lesser, int nE, cudaStream_t st, int e_off = 0);
+// Blocks of at most this many rows are factorised or inverted by thread
+// blocks of 128 threads (256 up to twice that, 512 above): per-step barriers
+// and pivot searches then span fewer warps, and more blocks share an SM.
+constexpr int kSmallBlock = 128;
 // df = 1: float-float arithmetic; in_smem = 1: the block is held in shared
 // memory (every op of the launch must have s <= invert_smem_max())
 void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_base, int nE,
