@@ -101,6 +101,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-side-paths", action="store_true",
                     help="skip the one-step measurement of the other precision paths")
+    ap.add_argument("--ldl", action="store_true",
+                    help="the symmetric LDL^T elimination on the mixed paths too (FIND_FLAG_LDL)")
     ap.add_argument("--path", choices=["fp64", "mixed", "mixed_ff"], default="mixed_ff",
                     help="fp64: every step in FP64 (LDL^T elimination); mixed: below the two "
                          "top tree levels the Schur and leaf products on the tensor cores "
@@ -436,6 +438,7 @@ def bench_config(args, ws, B, extra=None):
     """The `config` object of both arms (the same workload description)."""
     cfg = {"workload": WORKLOAD if args.mesh == "256x1024" else f"{args.mesh} profiling case",
            "energies_per_step": B, "leaf": 8, "path": args.path,
+           "elimination": "LDL^T" if (args.ldl or args.path == "fp64") else "LU",
            "parallelism": f"energy-sharded x{ws}, no data-path collective"}
     cfg.update(extra or {})
     return cfg
@@ -512,7 +515,7 @@ def main():
     Es = W.c5_bench_energies()
     B = args.batch
     f = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=B, precision=args.path,
-                         energy_group=B)
+                         energy_group=B, ldl=True if args.ldl else None)
     n, nb = mesh.n, f.n_bonds
     dev = f"cuda:{device}"
     # timed step k takes batch k of the grid; warm-up steps take the batches after them

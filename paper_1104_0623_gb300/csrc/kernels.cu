@@ -443,6 +443,113 @@ __device__ void gauss_jordan(T* a, int ld, int s, T* colk, T* rowk, int* piv, in
   }
 }
 
+// Gauss-Jordan as above, blocked by panels of PW pivot steps: inside a panel
+// each step updates only the panel's own columns and its pivot row; the
+// other columns take the panel's PW steps together once it is done (the
+// multipliers of every row kept in coef, the scaled pivot rows in prow).
+// Every entry sees the same operations in the same order as in
+// gauss_jordan, so the result is identical; the block crosses memory once per
+// panel instead of once per step.  Shared memory: prow PW x s, coef s x PW.
+template <class X, int PW, class T>
+__device__ void gauss_jordan_panel(T* a, int ld, int s, T* prow, T* coef, int* piv, int* status,
+                                   int energy) {
+  __shared__ typename X::M red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int sh_p;
+  __shared__ T sh_pinv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int nt = blockDim.x;
+  for (int k0 = 0; k0 < s; k0 += PW) {
+    const int w = min(PW, s - k0), k1 = k0 + w;
+    for (int t = 0; t < w; ++t) {
+      const int k = k0 + t;
+      const int p = pivot_row<X>(a, ld, k, s, red_v, red_i, &sh_p);
+      if (tid == 0) piv[k] = p;
+      if (p != k) {  // whole rows, with the multipliers of their pending steps
+        for (int j = tid; j < s; j += nt) {
+          T t0 = a[(int64_t)k * ld + j];
+          a[(int64_t)k * ld + j] = a[(int64_t)p * ld + j];
+          a[(int64_t)p * ld + j] = t0;
+        }
+        for (int q = tid; q < t; q += nt) {
+          T t0 = coef[k * PW + q];
+          coef[k * PW + q] = coef[p * PW + q];
+          coef[p * PW + q] = t0;
+        }
+      }
+      __syncthreads();
+      // the pivot row takes the panel's earlier steps on its other columns
+      for (int j = tid; j < s; j += nt) {
+        if (j >= k0 && j < k1) continue;
+        T v = a[(int64_t)k * ld + j];
+        for (int q = 0; q < t; ++q) v = X::fms(coef[k * PW + q], prow[q * s + j], v);
+        a[(int64_t)k * ld + j] = v;
+      }
+      __syncthreads();
+      if (tid == 0) {  // the pivot reciprocal, once per step, in FP64 (Smith)
+        const T pv = a[(int64_t)k * ld + k];
+        cplx pinv = cmk(0, 0);
+        if (X::is_zero(pv)) atomicMin(status, energy);
+        else pinv = crecip(X::to(pv));
+        sh_pinv = X::from(pinv);
+      }
+      __syncthreads();
+      const T pinv = sh_pinv;
+      for (int j = tid; j < s; j += nt) {
+        T v = (j == k) ? pinv : X::scale(a[(int64_t)k * ld + j], pinv);
+        prow[t * s + j] = v;
+        a[(int64_t)k * ld + j] = v;
+      }
+      __syncthreads();
+      // every other row: its multiplier, and this step on the panel's columns
+      for (int i = tid; i < s; i += nt) {
+        if (i == k) continue;
+        T* row = a + (int64_t)i * ld;
+        const T m = row[k];
+        coef[i * PW + t] = m;
+        for (int j = k0; j < k1; ++j) row[j] = X::fms(m, prow[t * s + j], j == k ? X::zero() : row[j]);
+      }
+      __syncthreads();
+    }
+    // the panel's steps on every other column, a warp per row (a pivot row
+    // of the panel takes only the steps after its own)
+    for (int i = warp; i < s; i += nwarp) {
+      const int q0 = (i >= k0 && i < k1) ? i - k0 + 1 : 0;
+      if (q0 >= w) continue;
+      T c[PW];
+#pragma unroll
+      for (int q = 0; q < PW; ++q)
+        if (q >= q0 && q < w) c[q] = coef[i * PW + q];
+      T* row = a + (int64_t)i * ld;
+      for (int j = lane; j < s; j += 64) {  // two independent chains in flight
+        const int j2 = j + 32;
+        const bool on0 = !(j >= k0 && j < k1), on1 = j2 < s && !(j2 >= k0 && j2 < k1);
+        T v0 = on0 ? row[j] : X::zero(), v1 = on1 ? row[j2] : X::zero();
+#pragma unroll
+        for (int q = 0; q < PW; ++q)
+          if (q >= q0 && q < w) {
+            if (on0) v0 = X::fms(c[q], prow[q * s + j], v0);
+            if (on1) v1 = X::fms(c[q], prow[q * s + j2], v1);
+          }
+        if (on0) row[j] = v0;
+        if (on1) row[j2] = v1;
+      }
+    }
+    __syncthreads();
+  }
+  // undo the row interchanges as column interchanges, last first
+  for (int k = s - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int i = tid; i < s; i += nt) {
+        T t0 = a[(int64_t)i * ld + k];
+        a[(int64_t)i * ld + k] = a[(int64_t)i * ld + p];
+        a[(int64_t)i * ld + p] = t0;
+      }
+    __syncthreads();
+  }
+}
+
 // Rewrites the leading s x s block of a complex128 matrix in the storage of
 // arithmetic X (a no-op for FP64), or back.
 template <class X>
@@ -468,11 +575,16 @@ __device__ __forceinline__ void from_work(cplx* a, int ld, int s) {
   }
 }
 
-// Inversion in global memory, one CTA per (op, energy).
+// Inversion in global memory, one CTA per (op, energy): blocked in panels of
+// kInvPanel steps up to kInvPanelMax rows (the panel's rows and multipliers
+// in shared memory), step by step above.
+constexpr int kInvPanel = 4;
+constexpr int kInvPanelMax = 1024;
+
 template <bool DF>
 __global__ void __launch_bounds__(kInvThreads) k_invert(const InvOp* __restrict__ ops,
                                                         int* __restrict__ status, int e_base,
-                                                        int e_off) {
+                                                        int e_off, int panel) {
   typedef GA<DF> X;
   typedef typename X::T T;
   const InvOp op = ops[blockIdx.x];
@@ -481,11 +593,18 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(const InvOp* __restrict_
   if (s == 0) return;
   cplx* a = op.M + (int64_t)e * op.estride;
   extern __shared__ double2 inv_smem[];
-  T* colk = reinterpret_cast<T*>(inv_smem);
-  T* rowk = colk + s;
-  int* piv = reinterpret_cast<int*>(rowk + s);
   to_work<X>(a, ld, s);
-  gauss_jordan<X>(reinterpret_cast<T*>(a), ld, s, colk, rowk, piv, status, e_base + e);
+  if (panel) {  // the launch's largest block fits the panel layout
+    T* prow = reinterpret_cast<T*>(inv_smem);
+    T* coef = prow + (int64_t)kInvPanel * s;
+    int* piv = reinterpret_cast<int*>(coef + (int64_t)kInvPanel * s);
+    gauss_jordan_panel<X, kInvPanel>(reinterpret_cast<T*>(a), ld, s, prow, coef, piv, status, e_base + e);
+  } else {
+    T* colk = reinterpret_cast<T*>(inv_smem);
+    T* rowk = colk + s;
+    int* piv = reinterpret_cast<int*>(rowk + s);
+    gauss_jordan<X>(reinterpret_cast<T*>(a), ld, s, colk, rowk, piv, status, e_base + e);
+  }
   from_work<X>(a, ld, s);
 }
 
@@ -659,7 +778,19 @@ __global__ void __launch_bounds__(kInvThreads, 2) k_lu_panel(const InvOp* __rest
 #pragma unroll
       for (int t = 0; t < PW; ++t)
         if (t < w) l[t] = row[k0 + t];
-      for (int j = k1 + lane; j < s; j += 32) {
+      int j = k1 + lane;
+      for (; j + 32 < s; j += 64) {  // two independent chains in flight
+        T v0 = row[j], v1 = row[j + 32];
+#pragma unroll
+        for (int t = 0; t < PW; ++t)
+          if (t < w) {
+            v0 = X::fms(l[t], urow[t * s + j], v0);
+            v1 = X::fms(l[t], urow[t * s + j + 32], v1);
+          }
+        row[j] = v0;
+        row[j + 32] = v1;
+      }
+      if (j < s) {
         T v = row[j];
 #pragma unroll
         for (int t = 0; t < PW; ++t)
@@ -713,7 +844,8 @@ __device__ __forceinline__ double cabs1(cplx v) { return fabs(v.x) + fabs(v.y); 
 // alpha sigma; else the 2x2 pivot on {k, r}.  |.| is |re| + |im|.  Only the
 // lower triangle is read and updated (half the flops of the LU, Sec. 4.2).
 // FP64, or float-float (the block rewritten in place as float-float words
-// during the factorisation, like k_lu).
+// during the factorisation, like k_lu).  Blocks of up to kLdlPanelMax rows
+// are factorised in panels (ldl_panel, below), larger ones step by step.
 // On exit: P M P^T = T D T^T with T unit lower, stored below the diagonal
 // (zero at the sub-diagonal of each 2x2 block) and mirrored above it (the
 // forward sweep of k_trsm reads T^T there), ones on the diagonal; D in dv
@@ -728,10 +860,186 @@ __device__ __forceinline__ cplx neg_of(cplx v) { return cmk(-v.x, -v.y); }
 template <>
 __device__ __forceinline__ float4 neg_of(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
 
+// The same factorisation blocked by panels of at least PW columns: inside a
+// panel no step updates the trailing triangle; a column takes the panel's
+// earlier steps when it is needed (the candidate pivot column k, and row and
+// column r for the pivot test, formed aside in wk and wr), and the trailing
+// triangle takes all of the panel's steps at once at its end.  The unscaled
+// pivot columns are kept in C (s x (PW + 1), by row), so a symmetric
+// interchange swaps two rows of C with the rows of A.  Each entry sees the
+// same products as in the step-by-step kernel, but an entry that an
+// interchange moves across the diagonal takes its update from the other
+// triangle's operands (l_j c_i for l_i c_j), so the factors agree with it to
+// rounding, not bit for bit; the pivot decisions use the same updated values.
+template <class X, int PW, class T>
+__device__ void ldl_panel(T* a, int ld, int s, int* piv, int* kind, cplx* dv, T* C, T* wk, T* wr,
+                          int* status, int energy, double* red_v, int* red_i) {
+  constexpr int CW = PW + 1;  // a panel ends after PW columns, or PW + 1 with a closing 2x2 block
+  __shared__ int lcol[CW];
+  __shared__ int sh_kp, sh_step;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int nt = blockDim.x;
+  const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+  auto A = [&](int i, int j) -> T& { return a[(int64_t)i * ld + j]; };
+  // entry (i, j), i >= j, of the lower triangle with the panel's steps applied
+  auto upd = [&](int i, int j, int nc) {
+    T v = A(i, j);
+    for (int c = 0; c < nc; ++c) v = X::fms(A(i, lcol[c]), C[j * CW + c], v);
+    return v;
+  };
+  int k = 0;
+  while (k < s) {
+    int nc = 0;
+    while (k < s && nc < PW) {
+      for (int i = k + tid; i < s; i += nt) wk[i] = upd(i, k, nc);
+      __syncthreads();
+      double colmax;
+      int imax;
+      block_argmax(k + 1, s, [&](int i) { return (double)X::mag(wk[i]); }, red_v, red_i, colmax, imax);
+      const double absakk = (double)X::mag(wk[k]);
+      int kp = k, step = 1;
+      if (colmax > 0.0 && absakk < alpha * colmax) {
+        for (int j = k + tid; j < s; j += nt)
+          wr[j] = j == k ? wk[imax] : (j < imax ? upd(imax, j, nc) : upd(j, imax, nc));
+        __syncthreads();
+        double rm1, rm2;
+        int i1, i2;
+        block_argmax(k, imax, [&](int j) { return (double)X::mag(wr[j]); }, red_v, red_i, rm1, i1);
+        block_argmax(imax + 1, s, [&](int j) { return (double)X::mag(wr[j]); }, red_v, red_i, rm2, i2);
+        const double rowmax = fmax(rm1, rm2);
+        if (absakk * rowmax >= alpha * colmax * colmax) {
+          kp = k;
+        } else if ((double)X::mag(wr[imax]) >= alpha * rowmax) {
+          kp = imax;
+        } else {
+          kp = imax;
+          step = 2;
+        }
+      }
+      if (tid == 0) { sh_kp = kp; sh_step = step; }
+      __syncthreads();
+      kp = sh_kp;
+      step = sh_step;
+      const int kk = k + step - 1;
+      if (!(step == 1 && kp != k))  // column k stays: it takes its updated values
+        for (int i = k + tid; i < s; i += nt) A(i, k) = wk[i];
+      __syncthreads();
+      if (kp != kk) {
+        if (tid == 0) {
+          const T t = A(kk, kk);
+          A(kk, kk) = A(kp, kp);
+          A(kp, kp) = t;
+        }
+        for (int j = kk + 1 + tid; j < kp; j += nt) {
+          const T t = A(j, kk);
+          A(j, kk) = A(kp, j);
+          A(kp, j) = t;
+        }
+        for (int i = kp + 1 + tid; i < s; i += nt) {
+          const T t = A(i, kk);
+          A(i, kk) = A(i, kp);
+          A(i, kp) = t;
+        }
+        for (int j = tid; j < kk; j += nt) {
+          const T t = A(kk, j);
+          A(kk, j) = A(kp, j);
+          A(kp, j) = t;
+        }
+        for (int c = tid; c < nc; c += nt) {
+          const T t = C[kk * CW + c];
+          C[kk * CW + c] = C[kp * CW + c];
+          C[kp * CW + c] = t;
+        }
+      }
+      if (tid == 0) {
+        piv[k] = (step == 1) ? kp : k;
+        kind[k] = step == 1 ? 0 : 1;
+        if (step == 2) {
+          piv[k + 1] = kp;
+          kind[k + 1] = 2;
+        }
+      }
+      __syncthreads();
+      if (step == 1) {
+        if (kp != k) {  // the new column k takes the panel's steps
+          for (int i = k + tid; i < s; i += nt) wk[i] = upd(i, k, nc);
+          __syncthreads();
+          for (int i = k + tid; i < s; i += nt) A(i, k) = wk[i];
+          __syncthreads();
+        }
+        const cplx d = X::to(A(k, k));
+        const bool zero = d.x == 0.0 && d.y == 0.0;
+        const T r = X::from(zero ? cmk(0, 0) : crecip(d));
+        if (tid == 0) {
+          dv[k] = d;
+          dv[s + k] = cmk(0, 0);
+          if (zero) atomicMin(status, energy);
+          lcol[nc] = k;
+        }
+        for (int i = k + 1 + tid; i < s; i += nt) {
+          const T c = A(i, k);
+          C[i * CW + nc] = c;
+          A(i, k) = X::scale(c, r);
+        }
+      } else {
+        for (int i = k + 1 + tid; i < s; i += nt) wk[i] = upd(i, k + 1, nc);
+        __syncthreads();
+        for (int i = k + 1 + tid; i < s; i += nt) A(i, k + 1) = wk[i];
+        __syncthreads();
+        const cplx d11 = X::to(A(k, k)), d21 = X::to(A(k + 1, k)), d22 = X::to(A(k + 1, k + 1));
+        const cplx det = csub(cmul(d11, d22), cmul(d21, d21));
+        const bool zero = det.x == 0.0 && det.y == 0.0;
+        const cplx r = zero ? cmk(0, 0) : crecip(det);
+        const T e11 = X::from(cmul(d22, r)), e22 = X::from(cmul(d11, r));
+        const T e21 = X::from(cmk(-(cmul(d21, r).x), -(cmul(d21, r).y)));
+        if (tid == 0) {
+          dv[k] = d11;
+          dv[k + 1] = d22;
+          dv[s + k] = d21;
+          dv[s + k + 1] = cmk(0, 0);
+          if (zero) atomicMin(status, energy);
+          lcol[nc] = k;
+          lcol[nc + 1] = k + 1;
+        }
+        for (int i = k + 2 + tid; i < s; i += nt) {
+          const T x1 = A(i, k), x2 = A(i, k + 1);
+          C[i * CW + nc] = x1;
+          C[i * CW + nc + 1] = x2;
+          A(i, k) = X::fms(x2, neg_of(e21), X::scale(x1, e11));
+          A(i, k + 1) = X::fms(x2, neg_of(e22), X::scale(x1, e21));
+        }
+        __syncthreads();
+        if (tid == 0) A(k + 1, k) = X::zero();  // T is the identity on the 2x2 block
+      }
+      __syncthreads();
+      nc += step;
+      k += step;
+    }
+    // the panel's steps on the trailing triangle, a warp per row
+    for (int i = k + warp; i < s; i += nwarp) {
+      T l[CW];
+#pragma unroll
+      for (int c = 0; c < CW; ++c)
+        if (c < nc) l[c] = A(i, lcol[c]);
+      T* row = a + (int64_t)i * ld;
+      for (int j = k + lane; j <= i; j += 32) {
+        T v = row[j];
+#pragma unroll
+        for (int c = 0; c < CW; ++c)
+          if (c < nc) v = X::fms(l[c], C[j * CW + c], v);
+        row[j] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+constexpr int kLdlPanel = 4;
+constexpr int kLdlPanelMax = 1024;
+
 template <bool DF>
-__global__ void __launch_bounds__(kInvThreads) k_ldl(const InvOp* __restrict__ ops,
+__global__ void __launch_bounds__(kInvThreads, 2) k_ldl(const InvOp* __restrict__ ops,
                                                      int* __restrict__ status, int e_base,
-                                                     int e_off) {
+                                                     int e_off, int panel) {
   typedef GA<DF> X;
   typedef typename X::T T;
   const InvOp op = ops[blockIdx.x];
@@ -754,7 +1062,13 @@ __global__ void __launch_bounds__(kInvThreads) k_ldl(const InvOp* __restrict__ o
   T* a = reinterpret_cast<T*>(g);
   auto A = [&](int i, int j) -> T& { return a[(int64_t)i * ld + j]; };
   auto mag = [&](int i, int j) { return (double)X::mag(A(i, j)); };
-  int k = 0;
+  if (panel) {  // the launch's largest block fits C, wk and wr in shared memory
+    T* C = reinterpret_cast<T*>(ldl_smem);
+    T* wk = C + (int64_t)s * (kLdlPanel + 1);
+    T* wr = wk + s;
+    ldl_panel<X, kLdlPanel>(a, ld, s, piv, kind, dv, C, wk, wr, status, e_base + e, red_v, red_i);
+  }
+  int k = panel ? s : 0;
   while (k < s) {
     double colmax;
     int imax;
@@ -1128,7 +1442,19 @@ __device__ __forceinline__ void rank_update(T* Y, const cplx* a, int ld, int s, 
     for (int t = 0; t < W; ++t)
       if (t < w) u[t] = fac_in<X, FF>(a + (int64_t)(j0 + t) * ld + i);
     const int r1 = min(rows, (rg + 1) * rpt);
-    for (int r = rg * rpt; r < r1; ++r) {
+    int r = rg * rpt;
+    for (; r + 1 < r1; r += 2) {  // two independent chains in flight
+      T v0 = Y[r * s + i], v1 = Y[(r + 1) * s + i];
+#pragma unroll
+      for (int t = 0; t < W; ++t)
+        if (t < w) {
+          v0 = X::fms(Y[r * s + j0 + t], u[t], v0);
+          v1 = X::fms(Y[(r + 1) * s + j0 + t], u[t], v1);
+        }
+      Y[r * s + i] = v0;
+      Y[(r + 1) * s + i] = v1;
+    }
+    if (r < r1) {
       T v = Y[r * s + i];
 #pragma unroll
       for (int t = 0; t < W; ++t)
@@ -1139,7 +1465,7 @@ __device__ __forceinline__ void rank_update(T* Y, const cplx* a, int ld, int s, 
 }
 
 template <bool DF, bool FF, bool LDL>
-__global__ void __launch_bounds__(512) k_trsm(const TrsmOp* __restrict__ ops,
+__global__ void __launch_bounds__(256) k_trsm(const TrsmOp* __restrict__ ops,
                                               const int* __restrict__ tile_op, int rb, int e_off) {
   typedef TrsmArith<DF> X;
   typedef typename X::T T;
@@ -1343,7 +1669,8 @@ void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_bas
   if (nops == 0 || max_s == 0) return;
   static bool attr_set = false;
   if (!attr_set) {
-    const int glob = (int)((size_t)kMaxInvert * (2 * sizeof(cplx) + sizeof(int)));
+    const int glob = (int)std::max((size_t)kMaxInvert * (2 * sizeof(cplx) + sizeof(int)),
+                                   (size_t)kInvPanelMax * (2 * kInvPanel * sizeof(cplx) + sizeof(int)));
     const int sm = (int)((size_t)kInvSmemMax * kInvSmemMax * sizeof(cplx) +
                          (size_t)kInvSmemMax * (2 * sizeof(cplx) + sizeof(int)));
     cudaFuncSetAttribute(k_invert<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, glob);
@@ -1360,12 +1687,16 @@ void launch_invert(const InvOp* ops, int nops, int max_s, int* status, int e_bas
     else
       k_invert_smem<false><<<grid, kInvThreads, smem, st>>>(ops, status, e_base, e_off);
   } else {
-    size_t smem = (size_t)max_s * (2 * sizeof(cplx) + sizeof(int));
-    const int nt = inv_threads(max_s);
+    // the panels' rows and multipliers (s <= kInvPanelMax), or a row and a column
+    size_t smem = max_s <= kInvPanelMax ? (size_t)max_s * (2 * kInvPanel * sizeof(cplx) + sizeof(int))
+                                        : (size_t)max_s * (2 * sizeof(cplx) + sizeof(int));
+    // 512 threads whatever the size: 128-thread blocks for the small bordered
+    // leaves measured slower than 512-thread ones
+    const int nt = kInvThreads, panel = max_s <= kInvPanelMax ? 1 : 0;
     if (df)
-      k_invert<true><<<grid, nt, smem, st>>>(ops, status, e_base, e_off);
+      k_invert<true><<<grid, nt, smem, st>>>(ops, status, e_base, e_off, panel);
     else
-      k_invert<false><<<grid, nt, smem, st>>>(ops, status, e_base, e_off);
+      k_invert<false><<<grid, nt, smem, st>>>(ops, status, e_base, e_off, panel);
   }
 }
 
@@ -1412,10 +1743,7 @@ void launch_trsm(const TrsmOp* ops, const int* tile_op, int ntiles, int rb, int 
   }
   size_t smem = (size_t)rb * max_s * sizeof(cplx) + (size_t)max_s * sizeof(int);
   dim3 grid(ntiles, nE);
-  // a block whose rows take more than half an SM's shared memory runs alone
-  // on its SM: give it 16 warps instead of 8 for the rank updates (the
-  // panel solves keep their 4 warps; every entry sees the same operations)
-  const int nt = smem > 113 * 1024 ? 512 : 256;
+  const int nt = 256;  // 512 threads for blocks alone on their SM measured slower
   if (ldl && df)
     k_trsm<true, false, true><<<grid, nt, smem, st>>>(ops, tile_op, rb, e_off);
   else if (ldl)
@@ -1433,18 +1761,19 @@ void launch_ldl(const InvOp* ops, int nops, int max_s, int* status, int e_base, 
   if (nops == 0 || max_s <= 0) return;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_ldl<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         2 * kMaxInvert * (int)sizeof(cplx));
-    cudaFuncSetAttribute(k_ldl<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         2 * kMaxInvert * (int)sizeof(float4));
+    const int most = std::max(2 * kMaxInvert, (kLdlPanel + 3) * kLdlPanelMax) * (int)sizeof(cplx);
+    cudaFuncSetAttribute(k_ldl<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_ldl<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     attr_set = true;
   }
   dim3 grid(nops, nE);
-  const int nt = inv_threads(max_s);
+  const int nt = inv_threads(max_s), panel = max_s <= kLdlPanelMax ? 1 : 0;
+  // panel: C (s x (kLdlPanel + 1)), wk and wr; step by step: two unscaled columns
+  const size_t smem = (size_t)max_s * (panel ? kLdlPanel + 3 : 2) * sizeof(cplx);
   if (df)
-    k_ldl<true><<<grid, nt, 2 * (size_t)max_s * sizeof(float4), st>>>(ops, status, e_base, e_off);
+    k_ldl<true><<<grid, nt, smem, st>>>(ops, status, e_base, e_off, panel);
   else
-    k_ldl<false><<<grid, nt, 2 * (size_t)max_s * sizeof(cplx), st>>>(ops, status, e_base, e_off);
+    k_ldl<false><<<grid, nt, smem, st>>>(ops, status, e_base, e_off, panel);
 }
 
 void launch_gemm(const GemmOp* ops, const int* tile_op, int ntiles, int big, int nE,

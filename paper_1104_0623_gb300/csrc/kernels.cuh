@@ -109,7 +109,7 @@ void launch_lead_dense(const cplx* sig_modes, const double* phi, int nx, int nE,
 // (grid.y = nE); independent energy groups can run on separate streams.
 void launch_assemble(const AsmOp* ops, const int* row_op, int nrows, const Pos* pos,
                      const DevProblem& P, int lesser, int nE, cudaStream_t st, int e_off = 0);
-// Blocks of at most this many rows are factorised or inverted by thread
+// Blocks of at most this many rows are factorised (LU, LDL^T) by thread
 // blocks of 128 threads (256 up to twice that, 512 above): per-step barriers
 // and pivot searches then span fewer warps, and more blocks share an SM.
 constexpr int kSmallBlock = 128;

@@ -105,12 +105,11 @@ struct Level {
   // index df + 2 * in_smem: [FP64, float-float, FP64 in shared memory,
   // float-float in shared memory]
   // inversion / factorisation classes: bit 0 float-float, bit 1 shared-memory
-  // inversion, bit 2 a leaf inversion of at most kSmallBlock nodes (launched
-  // on its own, with fewer threads per block)
-  size_t inv[6] = {0, 0, 0, 0, 0, 0};
-  int ninv[6] = {0, 0, 0, 0, 0, 0};
-  int inv_max[6] = {0, 0, 0, 0, 0, 0};
-  double fl_inv[6] = {0, 0, 0, 0, 0, 0};
+  // inversion
+  size_t inv[4] = {0, 0, 0, 0};
+  int ninv[4] = {0, 0, 0, 0};
+  int inv_max[4] = {0, 0, 0, 0};
+  double fl_inv[4] = {0, 0, 0, 0};
   Stage st[3];
   int nstages = 0;
 };
@@ -491,7 +490,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     Level lv;
     std::vector<findgb::AsmOp> asmops;
     std::vector<int> row_op;
-    std::vector<findgb::InvOp> inv[6];
+    std::vector<findgb::InvOp> inv[4];
     std::vector<findgb::TrsmOp> trs;
     std::vector<int> trs_map[2];
     std::vector<findgb::GemmOp> g[2];
@@ -626,7 +625,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     lv.nops = (int)ops.size();
     lv.asmops = arx.put(asmops);
     lv.row_op = arx.put(row_op);
-    for (int c = 0; c < 6; ++c) {
+    for (int c = 0; c < 4; ++c) {
       lv.inv[c] = arx.put(inv[c]);
       lv.ninv[c] = (int)inv[c].size();
     }
@@ -653,7 +652,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     lv.leaf = true;
     std::vector<findgb::AsmOp> asmops;
     std::vector<int> row_op;
-    std::vector<findgb::InvOp> inv[6];
+    std::vector<findgb::InvOp> inv[4];
     std::vector<findgb::GemmOp> g[2];
     std::vector<int> maps[2][6];
     std::vector<findgb::TcOp> tcq[2];
@@ -702,8 +701,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
       }
       {
         const bool leaf_ff = ff_all && p.cl[op.cluster].depth > top_levels;
-        const int lc = (leaf_ff ? 1 : 0) +
-                       (n <= inv_smem ? 2 : (n <= findgb::kSmallBlock ? 4 : 0));
+        const int lc = (leaf_ff ? 1 : 0) + (n <= inv_smem ? 2 : 0);
         inv[lc].push_back(findgb::InvOp{M, escr, n, n, nullptr, 0});
         lv.inv_max[lc] = std::max(lv.inv_max[lc], n);
         lv.fl_inv[lc] += 8.0 * (double)n * n * n;
@@ -749,7 +747,7 @@ void build_tables(find_handle* h, unsigned char* base, const Layout& L, int batc
     lv.nops = (int)p.leaf_ops.size();
     lv.asmops = arx.put(asmops);
     lv.row_op = arx.put(row_op);
-    for (int c = 0; c < 6; ++c) {
+    for (int c = 0; c < 4; ++c) {
       lv.inv[c] = arx.put(inv[c]);
       lv.ninv[c] = (int)inv[c].size();
     }
@@ -1014,11 +1012,11 @@ void run_level(find_handle* h, const Level& lv, const findgb::DevProblem& P, boo
                             P, lesser ? 1 : 0, nb, st, e_off);
   });
   if (lv.leaf) {
-    for (int c = 0; c < 6; ++c)
+    for (int c = 0; c < 4; ++c)
       if (lv.ninv[c] > 0)
         timed(h, st, (c & 1) ? 14 : 2, lv.fl_inv[c] * nb, 0.0, [&] {
           findgb::launch_invert(at<findgb::InvOp>(h, lv.inv[c]), lv.ninv[c], lv.inv_max[c], status,
-                                e_base, nb, st, e_off, c & 1, (c >> 1) == 1);
+                                e_base, nb, st, e_off, c & 1, c >> 1);
         });
   } else {
     for (int c = 0; c < 2; ++c)
@@ -1586,9 +1584,9 @@ void run_level_static(find_handle* h, const StaticView& sv, const Level& lv,
   findgb::launch_assemble(reinterpret_cast<const findgb::AsmOp*>(meta(lv.asmops)),
                           reinterpret_cast<const int*>(meta(lv.row_op)), lv.nrows, pos, P, 0, nb, st);
   if (lv.leaf) {
-    for (int c = 0; c < 6; ++c)
+    for (int c = 0; c < 4; ++c)
       findgb::launch_invert(reinterpret_cast<const findgb::InvOp*>(meta(lv.inv[c])), lv.ninv[c],
-                            lv.inv_max[c], status, e_base, nb, st, 0, c & 1, (c >> 1) == 1);
+                            lv.inv_max[c], status, e_base, nb, st, 0, c & 1, c >> 1);
   } else {
     for (int c = 0; c < 2; ++c) {
       if (sv.ldl == 1)
