@@ -59,7 +59,7 @@ TC_REAL_PER_PAIR = 4
 # (dram__bytes_read.sum + dram__bytes_write.sum), from the ncu captures
 # summarised in profiles/ (scaled as stated there); a class whose kernel
 # changed since its capture is left out.
-DOMINANT_TRAFFIC = {}
+DOMINANT_TRAFFIC = {"fftrsm": 5.646e9, "tcgemm": 1.829e10, "ffinvert": 9.100e11, "trsm": 7.871e8}
 
 
 def read_peaks():
@@ -101,6 +101,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-side-paths", action="store_true",
                     help="skip the one-step measurement of the other precision paths")
+    ap.add_argument("--energy-group", type=int, default=0,
+                    help="energies per concurrent stream group of a pass (0: the whole batch "
+                         "as one group, so that per-kernel event times do not overlap)")
     ap.add_argument("--ldl", action="store_true",
                     help="the symmetric LDL^T elimination on the mixed paths too (FIND_FLAG_LDL)")
     ap.add_argument("--path", choices=["fp64", "mixed", "mixed_ff"], default="mixed_ff",
@@ -515,7 +518,7 @@ def main():
     Es = W.c5_bench_energies()
     B = args.batch
     f = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=B, precision=args.path,
-                         energy_group=B, ldl=True if args.ldl else None)
+                         energy_group=args.energy_group or B, ldl=True if args.ldl else None)
     n, nb = mesh.n, f.n_bonds
     dev = f"cuda:{device}"
     # timed step k takes batch k of the grid; warm-up steps take the batches after them
@@ -612,7 +615,8 @@ def main():
            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.path], "data": "synthetic",
            "config": bench_config(args, ws, B, {
-               "energy_groups_per_pass": 1, "distinct_timed_energies": distinct,
+               "energy_groups_per_pass": -(-B // (args.energy_group or B)),
+               "distinct_timed_energies": distinct,
                "l2": f"inputs larger than L2: {f.workspace_bytes(B) / 2**30:.1f} GiB resident U/R "
                      f"and scratch per step"}),
            "clocks": clk, "n_sm": n_sm, "gpu_launches": sum(p["launches"] for p in prof),

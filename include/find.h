@@ -237,6 +237,14 @@ int find_solve_diag(find_handle* h, const double* E, int nE,
  *                      x-bonds (x,y)->(x+1,y) [y*(nx-1)+x]; stencil 9 adds
  *                      (x,y)->(x+1,y+1) and (x+1,y)->(x,y+1)
  *                      [y*(nx-1)+x, y<ny-1] in that order.
+ *
+ * Sigma< sparsity (Sec. 4.3): without a node-diagonal term, Sigma< is zero
+ * away from the contact columns y = 0 and y = ny - 1, so the upward merges of
+ * clusters with no contact node skip their Sigma update (R = 0 exactly) and
+ * the leaves with no contact node run their G< products over the nonzero
+ * block only.  The first call that passes sigma_lesser_diag rebuilds the
+ * handle's workspace and tables to run every update; they then
+ * serve all later calls of the handle.
  */
 int find_solve_lesser(find_handle* h, const double* E, int nE,
                       const double* sigmaL, const double* sigmaR,
