@@ -59,7 +59,7 @@ TC_REAL_PER_PAIR = 4
 # (dram__bytes_read.sum + dram__bytes_write.sum), from the ncu captures
 # summarised in profiles/ (scaled as stated there); a class whose kernel
 # changed since its capture is left out.
-DOMINANT_TRAFFIC = {"fftrsm": 5.646e9, "tcgemm": 1.829e10, "ffinvert": 9.100e11, "trsm": 7.871e8}
+DOMINANT_TRAFFIC = {"fftrsm": 5.650e9, "tcgemm": 1.825e10, "ffinvert": 9.089e11, "trsm": 7.863e8}
 
 
 def read_peaks():
@@ -630,7 +630,7 @@ def main():
     if args.mesh == "256x1024" and rank == 0:
         idx, Eg, norms, rows = refined_batch()
         g = F.Find.from_mesh(mesh, leaf=8, device=device, max_batch=B, precision=args.path,
-                             energy_group=B)
+                             energy_group=B, ldl=True if args.ldl else None)
         G, Gl, _ = g.solve_lesser(torch.tensor(Eg[:B], dtype=torch.complex128, device=dev), bonds=False)
         g.close()
         accuracy[args.path] = accuracy_vs_refined(idx, G.cpu().numpy(), Gl.cpu().numpy(), norms, rows)

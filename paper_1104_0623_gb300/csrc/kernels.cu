@@ -1402,9 +1402,10 @@ struct TrsmArith<true> {
   }
 };
 
-constexpr int kTrsmW = 8;        // columns per panel
+constexpr int kTrsmW = 16;       // columns per panel (8 measured slower: twice the barriers,
+                                 // and half the block idle in each panel solve)
 constexpr int kTrsmRowsMax = 16; // rows per CTA at most (24 measured slower)
-constexpr int kPanelThreads = kTrsmW * kTrsmRowsMax;  // 4 whole warps
+constexpr int kPanelThreads = kTrsmW * kTrsmRowsMax;  // 8 whole warps: the block
 static_assert(kPanelThreads % 32 == 0 && 32 % kTrsmW == 0, "panel lanes must tile warps");
 
 // Entries of the LU factors of M(S,S).  FF: the float-float LU left them as
@@ -1430,36 +1431,39 @@ __device__ __forceinline__ cplx fac_wide(const cplx* p) {
 template <class X, bool FF, class T>
 __device__ __forceinline__ void rank_update(T* Y, const cplx* a, int ld, int s, int rows, int j0,
                                             int w, int c0, int c1, int tid, int nt) {
-  constexpr int W = kTrsmW;
+  constexpr int WC = 8;  // factor rows held in registers at a time
   const int C = c1 - c0;
   if (C <= 0) return;
   const int tpc = C >= nt ? 1 : max(1, min(rows, nt / C));  // threads per column
   const int rpt = (rows + tpc - 1) / tpc;                   // rows per thread
   for (int it = tid; it < C * tpc; it += nt) {
     const int i = c0 + it / tpc, rg = it % tpc;
-    T u[W];
-#pragma unroll
-    for (int t = 0; t < W; ++t)
-      if (t < w) u[t] = fac_in<X, FF>(a + (int64_t)(j0 + t) * ld + i);
     const int r1 = min(rows, (rg + 1) * rpt);
-    int r = rg * rpt;
-    for (; r + 1 < r1; r += 2) {  // two independent chains in flight
-      T v0 = Y[r * s + i], v1 = Y[(r + 1) * s + i];
+    for (int t0 = 0; t0 < w; t0 += WC) {  // the panel's rows in order, WC at a time
+      const int wc = min(WC, w - t0);
+      T u[WC];
 #pragma unroll
-      for (int t = 0; t < W; ++t)
-        if (t < w) {
-          v0 = X::fms(Y[r * s + j0 + t], u[t], v0);
-          v1 = X::fms(Y[(r + 1) * s + j0 + t], u[t], v1);
-        }
-      Y[r * s + i] = v0;
-      Y[(r + 1) * s + i] = v1;
-    }
-    if (r < r1) {
-      T v = Y[r * s + i];
+      for (int t = 0; t < WC; ++t)
+        if (t < wc) u[t] = fac_in<X, FF>(a + (int64_t)(j0 + t0 + t) * ld + i);
+      int r = rg * rpt;
+      for (; r + 1 < r1; r += 2) {  // two independent chains in flight
+        T v0 = Y[r * s + i], v1 = Y[(r + 1) * s + i];
 #pragma unroll
-      for (int t = 0; t < W; ++t)
-        if (t < w) v = X::fms(Y[r * s + j0 + t], u[t], v);
-      Y[r * s + i] = v;
+        for (int t = 0; t < WC; ++t)
+          if (t < wc) {
+            v0 = X::fms(Y[r * s + j0 + t0 + t], u[t], v0);
+            v1 = X::fms(Y[(r + 1) * s + j0 + t0 + t], u[t], v1);
+          }
+        Y[r * s + i] = v0;
+        Y[(r + 1) * s + i] = v1;
+      }
+      if (r < r1) {
+        T v = Y[r * s + i];
+#pragma unroll
+        for (int t = 0; t < WC; ++t)
+          if (t < wc) v = X::fms(Y[r * s + j0 + t0 + t], u[t], v);
+        Y[r * s + i] = v;
+      }
     }
   }
 }
