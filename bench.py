@@ -101,6 +101,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-side-paths", action="store_true",
                     help="skip the one-step measurement of the other precision paths")
+    ap.add_argument("--graph-study", action="store_true",
+                    help="serve small meshes with and without CUDA-graph replay and exit")
     ap.add_argument("--energy-group", type=int, default=0,
                     help="energies per concurrent stream group of a pass (0: the whole batch "
                          "as one group, so that per-kernel event times do not overlap)")
@@ -332,6 +334,31 @@ def serving_study(device, n_requests, lam_fracs, n_control, precision="mixed_ff"
             "by_lambda": by_lambda, **controls}
 
 
+def graph_study(device, n_requests=48, precision="mixed_ff", chunk=8, slots=4):
+    """Serving small meshes with and without CUDA-graph replay of each chunk:
+    four small device meshes (16-64 x 16-128, 5-point), n_requests requests
+    drawn over them with 8-32 energies each, all arriving at once (closed
+    loop); each variant runs the stream twice and reports the second run (the
+    plans, and the captured graphs, built by the first)."""
+    from paper_1104_0623_gb300.serve import GpuBackend, Request, Server, summarize
+    rng = np.random.default_rng(4104)
+    meshes = [W.Mesh(int(rng.integers(16, 65)), int(rng.integers(16, 129)), 5, 1.0, 0.0, -0.5, 0.5, 1104 + k)
+              for k in range(4)]
+    reqs = [Request(k, 0.0, meshes[int(rng.integers(0, 4))],
+                    W.energy_grid(0.2, 3.8, int(rng.integers(8, 33)))) for k in range(n_requests)]
+    out = {"scenario": f"{n_requests} requests over 4 meshes "
+                       f"({', '.join(f'{m.nx}x{m.ny}' for m in meshes)}), 8-32 energies, "
+                       f"{precision} path, {slots} slots, {chunk}-energy chunks, closed loop"}
+    for name, gmax in (("eager", 0), ("graph", 1 << 30)):
+        srv = Server(GpuBackend(device, precision, chunk=chunk, graph_max_nodes=gmax), slots=slots, chunk=chunk)
+        srv.run(reqs)
+        sm = summarize(srv.run(reqs))
+        srv.close()
+        out[name] = {k: sm[k] for k in ("points_per_s", "p50_s", "p99_s")}
+        print(json.dumps({"partial": {name: out[name]}}), flush=True)
+    return out
+
+
 def crossover(device, sizes, n_energies=16):
     """FIND (FP64 with LDL^T, and the mixed path) against the recursive Green's
     function baseline (FP64) on square N x N 5-point meshes (V ~ U[-0.5, 0.5]),
@@ -498,6 +525,9 @@ def main():
 
     if args.crossover:
         crossover(device, [int(x) for x in args.crossover.split(",")])
+        return
+    if args.graph_study:
+        print(json.dumps(graph_study(device)), flush=True)
         return
     if args.serving_study:
         out = serving_study(device, args.serve_requests,

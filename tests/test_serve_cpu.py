@@ -113,3 +113,19 @@ def test_plans_are_built_without_stalling_running_requests():
     during = [t for t, k in be.solves if k == mesh_key(a.mesh) and t0 < t < t1]
     assert len(during) >= 5
     assert len(be.builds) == 2   # each plan built once
+
+
+
+def test_a_server_runs_a_second_stream_with_its_plans_cached():
+    be = FakeBackend(budget=1e9)
+    built = []
+    make = be.make_plan
+    be.make_plan = lambda mesh, energies=None: built.append(mesh_key(mesh)) or make(mesh, energies)
+    srv = Server(be, slots=2, chunk=4)
+    first = srv.run(make_requests())
+    n_plans = len(built)
+    second = srv.run(make_requests())
+    assert n_plans == 3 and len(built) == 3   # the second stream reuses every plan
+    for a, b in zip(first, second):
+        assert np.array_equal(a.diagG, b.diagG)
+    srv.close()
