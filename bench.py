@@ -627,6 +627,13 @@ def main():
     # measured copy peak
     hbm_peak = measured_hbm_gbs()
     for p in prof:
+        # DRAM bytes per launch from the full-size capture (where taken), and
+        # the rate they imply over this run's launches
+        if p["launches"] and p["name"] in DOMINANT_TRAFFIC and p["ms"] > 0:
+            tb = DOMINANT_TRAFFIC[p["name"]]
+            kernels[p["name"]]["traffic"] = tb
+            kernels[p["name"]]["traffic_gbs"] = tb * p["launches"] / (p["ms"] / 1e3) / 1e9
+    for p in prof:
         if p["launches"] and p["bytes"] > 0 and p["ms"] > 0:
             gbs = p["bytes"] / (p["ms"] / 1e3) / 1e9
             kernels[p["name"]]["achieved_gbs"] = gbs
