@@ -225,17 +225,21 @@ __device__ __forceinline__ cplx s_orig(const DevProblem& P, int e, int i, int j)
 }
 
 // ---------------------------------------------------------------- assembly
-// One CTA per (row of an op, group of kAsmEnergies energies): the row's
-// position entries (which source block and index, or the original A and
-// Sigma<) do not depend on the energy, so they are read once per CTA and
-// reused for every energy of the group.
+// A warp per (row of an op, group of kAsmEnergies energies), kAsmRows rows per
+// CTA: the row's position entries (which source block and index, or the
+// original A and Sigma<) do not depend on the energy, so they are read once
+// and reused for every energy of the group.  Rows are 20-1000 entries long; a
+// warp per row keeps short rows from leaving most of a CTA idle.
 constexpr int kAsmEnergies = 4;
+constexpr int kAsmRows = 8;
 
 __global__ void __launch_bounds__(256, 3) k_assemble(const AsmOp* __restrict__ ops,
                                                   const int* __restrict__ row_op,
                                                   const Pos* __restrict__ pos, DevProblem P,
-                                                  int lesser, int e_off, int nE) {
-  const int r = blockIdx.x;
+                                                  int lesser, int e_off, int nE, int nrows) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * kAsmRows + (threadIdx.x >> 5);  // a warp per row
+  if (r >= nrows) return;
   const AsmOp& op = ops[row_op[r]];
   const int n = op.n;
   const int p = r - op.row0;
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(256, 3) k_assemble(const AsmOp* __restrict__ o
   const int d = pp.src == 1 ? op.d1 : (pp.src == 2 ? op.d2 : 0);
   // Sigma_M of an op whose nodes carry no Sigma< is zero and not read: skipped
   const bool les = lesser && op.sig;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+  for (int q = lane; q < n; q += 32) {
     const Pos pq = pos[op.pos + q];
     if (pp.src != 0 && pq.src == pp.src) {
       // the group's source entries first (independent loads in flight), then
@@ -1657,8 +1661,8 @@ void launch_lead_dense(const cplx* sig_modes, const double* phi, int nx, int nE,
 void launch_assemble(const AsmOp* ops, const int* row_op, int nrows, const Pos* pos,
                      const DevProblem& P, int lesser, int nE, cudaStream_t st, int e_off) {
   if (nrows == 0 || nE == 0) return;
-  dim3 grid(nrows, (nE + kAsmEnergies - 1) / kAsmEnergies);
-  k_assemble<<<grid, 256, 0, st>>>(ops, row_op, pos, P, lesser, e_off, nE);
+  dim3 grid((nrows + kAsmRows - 1) / kAsmRows, (nE + kAsmEnergies - 1) / kAsmEnergies);
+  k_assemble<<<grid, 32 * kAsmRows, 0, st>>>(ops, row_op, pos, P, lesser, e_off, nE, nrows);
 }
 
 // Threads per block of the factorisations and inversions: every entry sees
